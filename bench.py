@@ -1,0 +1,365 @@
+"""Benchmark: PageRank GTEPS and fraction of the HBM roofline on one GB300,
+fused (nonblocking, whole loop on the GPU) vs op-by-op (blocking mode).
+
+Workload: R-MAT scale 22 (2^22 vertices, 2^26 raw edges, a,b,c,d =
+.57,.19,.19,.05, duplicates and self loops dropped, labels scrambled),
+FP32 ranks with an FP64 residual, damping 0.85, dangling rank spread
+uniformly, 50 fixed iterations, seed 1.  A step is one PageRank solve
+(50 fused iterations) on the graph resident in HBM; GTEPS = m x 50 / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  With --impl reference the FP64 CPU oracle (the
+baseline arm) is timed on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PageRank GTEPS & % HBM peak, fused vs op-by-op on 1 GB300, at L1 ≤1e-6 vs FP64"
+SCALE, EDGE_FACTOR, SEED, ITERS, DAMPING = 22, 16, 1, 50, 0.85
+WORKLOAD = ("R-MAT scale 22 (4,194,304 vertices, 67,108,864 raw edges, a=.57 b=.19 c=.19 d=.05, dedup, "
+            "no self loops), FP32 ranks, FP64 residual, damping 0.85, uniform dangling, 50 fixed iterations, seed 1")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _start_clock_sampler(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        return subprocess.Popen(cmd, stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def _clocks_summary(path, device_index):
+    sm, mx, reasons = [], [], set()
+    try:
+        with open(path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9 or parts[0] != str(device_index):
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                   parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+    except FileNotFoundError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """Baseline arm: the FP64 CPU oracle as it stands, on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+
+    src, dst = graphgen.rmat_edges(SCALE, EDGE_FACTOR, seed=SEED)
+    n = 1 << SCALE
+    ptr, col = oracle.build_at(n, src, dst)
+    outdeg = oracle.out_degree(ptr, col)
+    m = int(len(col))
+    # each step: 2 iterations of the oracle's pagerank on the full graph
+    iters_per_step = 2
+    for _ in range(args.warmup):
+        oracle.pagerank(ptr, col, outdeg, damping=DAMPING, tol=-1.0, itermax=iters_per_step, mode="uniform")
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.pagerank(ptr, col, outdeg, damping=DAMPING, tol=-1.0, itermax=iters_per_step, mode="uniform")
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = m * iters_per_step / t / 1e9
+    sample = f"{iters_per_step} FP64 oracle iterations per step on the full R-MAT scale 22 graph (CSR build untimed)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "iterations_per_step": iters_per_step},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_profile_case(args):
+    """A small run of the fused device loop for ncu captures: builds R-MAT
+    --scale, runs --warmup + --steps loops of --iters fused iterations."""
+    import torch
+
+    import graphgen
+    import paper_2509_14211_gb300 as grb
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
+
+    torch.cuda.set_device(0)
+    n = 1 << args.scale
+    src, dst = graphgen.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, args.loop_mode)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    m = grb.grb_matrix_nvals(AT)
+    P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+    for _ in range(args.warmup):
+        P.run(-1.0, args.iters, "device")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        P.run(-1.0, args.iters, "device")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"profile_case": True, "scale": args.scale, "n": n, "m": m, "iters": args.iters,
+                      "ms_per_loop": ms, "gteps": m * args.iters / (ms * 1e-3) / 1e9}), flush=True)
+    P.free()
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-oracle", action="store_true", help="skip the FP64 oracle (error and CPU baseline)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="profiling run: only the fused device loop, on --scale/--iters (no JSON contract)")
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--loop-mode", type=int, default=1, help="1 persistent kernel, 2 CUDA graph of fused kernels")
+    args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import graphgen
+    import paper_2509_14211_gb300 as grb
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
+
+    n = 1 << SCALE
+    src, dst = graphgen.rmat_edges(SCALE, EDGE_FACTOR, seed=SEED)
+    src_pin = torch.from_numpy(src).pin_memory()
+    dst_pin = torch.from_numpy(dst).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ------------------------------------------------------------ fused
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 1)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    m = grb.grb_matrix_nvals(AT)
+    P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+    for _ in range(args.warmup):
+        assert P.run(-1.0, ITERS, "device") == ITERS
+    clock_path = tempfile.mktemp(suffix=".csv")
+    sampler = _start_clock_sampler(clock_path)
+    time.sleep(0.3)
+    launches0 = grb.grb_context_stats(ctx)["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        P.run(-1.0, ITERS, "device")
+        ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = grb.grb_context_stats(ctx)["kernel_launches"] - launches0
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clocks_summary(clock_path, dev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    r_fused = P.rank().astype(np.float64)
+    rdiff = P.residual()
+    hist, _ = grb.grb_iterate_history(ctx)
+    value = ws * m * ITERS / (ms * 1e-3) / 1e9
+
+    # graph-of-kernels variant of the device loop
+    grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 2)
+    for _ in range(2):
+        P.run(-1.0, ITERS, "device")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        P.run(-1.0, ITERS, "device")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / 3
+    grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 1)
+
+    # host loop with per-wait fusion (the paper's nonblocking mode)
+    P.run(-1.0, 5, "host")
+    e0.record(stream)
+    P.run(-1.0, ITERS, "host")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    perwait_ms = e0.elapsed_time(e1)
+    P.free()
+
+    # ---------------------------------------------------------- unfused
+    ctxb = grb.grb_context_new(grb.GRB_BLOCKING)
+    ATb = grb.grb_matrix_build_csr(ctxb, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    Pb = PageRankProblem(ctxb, ATb, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+    Pb.run(-1.0, 5, "host")
+    ub0 = grb.grb_context_stats(ctxb)["kernel_launches"]
+    e0.record(stream)
+    Pb.run(-1.0, ITERS, "host")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    unfused_ms = e0.elapsed_time(e1)
+    unfused_launches = grb.grb_context_stats(ctxb)["kernel_launches"] - ub0
+    r_unfused = Pb.rank().astype(np.float64)
+    Pb.free()
+    grb.grb_free(ATb)
+    grb.grb_free(ctxb)
+
+    # -------------------------------------------------------------- e2e
+    # through the public API from pinned host COO: upload, CSR build, 50
+    # fused iterations, read the ranks back
+    e2e_ms = []
+    h2d = int(src_pin.numel() * 4 * 2)
+    d2h = n * 4
+    out_host = torch.empty(n, dtype=torch.float32).pin_memory()
+    for k in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        s_dev = src_pin.to("cuda", non_blocking=True)
+        d_dev = dst_pin.to("cuda", non_blocking=True)
+        A2 = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, s_dev, d_dev, None, BUILD_FLAGS)
+        P2 = PageRankProblem(ctx, A2, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+        P2.run(-1.0, ITERS, "device")
+        vals, _ = grb.grb_vector_extract_dense(P2.r, grb.GRB_FP32, present=False)
+        out_host.copy_(torch.from_numpy(vals))
+        barrier()
+        dt = time.perf_counter() - t0
+        P2.free()
+        grb.grb_free(A2)
+        del s_dev, d_dev
+        if k >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    e2e_t = sum(e2e_ms) / len(e2e_ms)
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+
+    # ---------------------------------------------------------- roofline
+    # algorithmic bytes of one launch of the persistent kernel: per body
+    # 4(n+1) row_ptr + 4m col_idx + 4n w gathered once + 4n d + 4n r_old +
+    # 4n r_new + 4n w_new + n/8 sink bits; the prologue reads r_0, d, the
+    # sink bits and writes w_0.
+    body_bytes = 4 * (n + 1) + 4 * m + 4 * n * 5 + n // 8
+    launch_bytes = ITERS * body_bytes + 12 * n + n // 8
+    peak, peak_kind = _peaks()
+    achieved = launch_bytes / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_kind, "kernel": "pr_persistent_kernel<float,float>",
+                "algorithmic_bytes_per_launch": launch_bytes}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "iterations": ITERS,
+                   "timing": "CUDA events on the launching stream; inputs larger than L2 (CSR 0.29 GB)",
+                   "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "e2e": {"value": ws * m * ITERS / (e2e_t * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": e2e_t,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "includes": "pinned COO upload, GPU CSR build, setup, 50 fused iterations, rank read-back"},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "fused_persistent_ms": ms,
+        "fused_graph_ms": graph_ms,
+        "fused_per_wait_host_loop_ms": perwait_ms,
+        "unfused_op_by_op_ms": unfused_ms,
+        "unfused_gpu_launches": unfused_launches,
+        "fused_vs_unfused": unfused_ms / ms,
+        "residual_after_50": rdiff,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and not args.no_oracle:
+        import oracle
+
+        t0 = time.perf_counter()
+        ptr, col = oracle.build_at(n, src, dst)
+        outdeg = oracle.out_degree(ptr, col)
+        t_build = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ref, _, ref_hist = oracle.pagerank(ptr, col, outdeg, damping=DAMPING, tol=-1.0, itermax=ITERS,
+                                           mode="uniform")
+        t_pr = time.perf_counter() - t0
+        out["l1_vs_fp64"] = float(np.sum(np.abs(r_fused - ref)))
+        out["l1_unfused_vs_fp64"] = float(np.sum(np.abs(r_unfused - ref)))
+        out["cpu_baseline"] = {"value": m * ITERS / t_pr / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                               "sample": f"the FP64 oracle's 50 iterations on the same graph ({t_pr:.1f} s; its "
+                                         f"CSR build, {t_build:.1f} s, untimed)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,298 @@
+/*
+ * grb.h -- C-ABI of the GB300 nonblocking GraphBLAS library (PageRank subset).
+ *
+ * The calls follow the GraphBLAS C API statement that the paper builds on
+ * (§II "Nonblocking execution"): destructive, output-first arguments; every
+ * call validates its arguments and returns at once; in NONBLOCKING mode the
+ * call only records a node of the program-order DAG (§II, §III-A), and the
+ * work runs when a result is needed (grb_wait, grb_scalar_get, an extract).
+ * At that point the planner fuses the pending DAG into as few GPU kernels as
+ * it can (§III-B: one fused loop per materialisation), looking kernels up by
+ * the DAG's signature (§III-C).  In BLOCKING mode every call completes and
+ * materialises its output before returning (§II), one GPU kernel per method.
+ * Both modes give the same results up to floating-point rounding order (§II).
+ *
+ * Conventions
+ *  - Handles are opaque and library-owned; release each with grb_free.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Device pointers are accepted where a flag says so.
+ *  - Device memory comes from the context's allocator callbacks (or the CUDA
+ *    stream-ordered allocator when none are given); all GPU work runs on the
+ *    context's stream.
+ *  - Errors: API errors (null handle, dimension or domain mismatch, invalid
+ *    value) are returned immediately and change nothing.  Execution errors
+ *    (out of memory, index out of range, device timeout) surface when the work
+ *    runs -- at grb_wait or a call that forces it -- and stick to the output
+ *    object; grb_error() returns the message.
+ *  - Indices are 32-bit (§IV uses 32-bit indices): n < 2^31, nnz < 2^31.
+ */
+#ifndef GRB_H
+#define GRB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status */
+typedef enum {
+    GRB_SUCCESS = 0,
+    GRB_NO_VALUE = 1,               /* scalar holds no value */
+    /* API errors (returned at once) */
+    GRB_NULL_POINTER = -1,
+    GRB_INVALID_VALUE = -2,
+    GRB_INVALID_INDEX = -3,
+    GRB_DOMAIN_MISMATCH = -4,
+    GRB_DIMENSION_MISMATCH = -5,
+    GRB_UNINITIALIZED_OBJECT = -6,
+    GRB_NOT_IMPLEMENTED = -7,
+    GRB_INVALID_OBJECT = -8,        /* object carries a sticky execution error */
+    /* execution errors (at wait; sticky on the object) */
+    GRB_OUT_OF_MEMORY = -101,
+    GRB_INDEX_OUT_OF_BOUNDS = -102,
+    GRB_DEVICE_ERROR = -103,
+    GRB_DEVICE_TIMEOUT = -104,      /* a bounded device-side wait ran out */
+    GRB_PANIC = -105
+} grb_info;
+
+/* §II: the two execution modes. */
+typedef enum { GRB_BLOCKING = 0, GRB_NONBLOCKING = 1 } grb_mode;
+
+/* Element types.  BF16 is a storage type: arithmetic on it runs in FP32. */
+typedef enum { GRB_INT32 = 1, GRB_FP32 = 2, GRB_FP64 = 3, GRB_BF16 = 4 } grb_type;
+
+/* Predefined binary operators.  MAX_DIV_BY carries a bound parameter k and
+ * computes (x, y) -> max(x / k, y), the operator the §IV PageRank listing
+ * uses to build the out-degree divisor. */
+typedef enum {
+    GRB_FIRST = 1, GRB_SECOND = 2, GRB_PLUS = 3, GRB_MINUS = 4, GRB_TIMES = 5,
+    GRB_DIV = 6, GRB_MAX = 7, GRB_MIN = 8, GRB_ABS_DIFF = 9, GRB_MAX_DIV_BY = 10
+} grb_opcode;
+
+typedef struct grb_binop {
+    int32_t opcode;   /* grb_opcode */
+    int32_t reserved; /* must be 0 */
+    double k;         /* parameter of GRB_MAX_DIV_BY; ignored otherwise */
+} grb_binop;
+
+/* Unary operators for grb_apply. */
+typedef enum { GRB_IDENTITY = 1, GRB_ABS = 2, GRB_AINV = 3, GRB_MINV = 4 } grb_unop;
+
+/* Monoids for reductions and semiring addition. */
+typedef enum { GRB_MONOID_PLUS = 1, GRB_MONOID_MAX = 2, GRB_MONOID_MIN = 3, GRB_MONOID_TIMES = 4 } grb_monoid;
+
+/* Semirings (add monoid, multiply operator).  PLUS_SECOND is the (+, (_,x)->x)
+ * semiring of the §IV listing's mxv; on an iso-1 pattern matrix PLUS_TIMES
+ * gives the same values. */
+typedef enum {
+    GRB_PLUS_TIMES = 1, GRB_PLUS_SECOND = 2, GRB_PLUS_FIRST = 3,
+    GRB_MAX_TIMES = 4, GRB_MIN_PLUS = 5, GRB_MAX_SECOND = 6
+} grb_semiring;
+
+/* Descriptor flags (bitwise OR). */
+enum {
+    GRB_DESC_DEFAULT = 0,
+    GRB_DESC_REPLACE = 1,     /* clear output entries outside the mask */
+    GRB_DESC_STRUCTURE = 2,   /* mask by presence, not by value */
+    GRB_DESC_COMPLEMENT = 4   /* use the complement of the mask */
+};
+typedef uint32_t grb_desc;
+
+/* grb_matrix_build_csr flags. */
+enum {
+    GRB_BUILD_TRANSPOSE = 1,   /* store A^T: row i lists the sources of edges j->i */
+    GRB_BUILD_DROP_SELF = 2,   /* drop self loops */
+    GRB_BUILD_DEDUP = 4,       /* drop duplicate (row, col) pairs */
+    GRB_BUILD_DEVICE_PTRS = 8  /* src/dst/vals are device pointers */
+};
+
+typedef enum { GRB_WAIT_COMPLETE = 0, GRB_WAIT_MATERIALIZE = 1 } grb_wait_mode;
+
+/* Context options (grb_context_set). */
+typedef enum {
+    GRB_OPT_FUSION = 1,        /* 1 (default): fuse at wait; 0: one kernel per method */
+    GRB_OPT_PERSISTENT = 2,    /* grb_iterate_end on a fused PageRank body:
+                                  0 = automatic (default), 1 = one persistent kernel
+                                  for all iterations, 2 = one fused kernel per
+                                  iteration captured in a CUDA graph, 3 = replay the
+                                  body from the host (per-wait fusion only) */
+    GRB_OPT_SPIN_LIMIT = 3,    /* iteration limit of device-side waits (>0) */
+    GRB_OPT_MIXED_SWITCH = 4,  /* residual below which the BF16 gather switches to
+                                  FP32, in units of 1e-9 (default 1e6, i.e. 1e-3) */
+    GRB_OPT_MIXED = 5          /* 1: FP32 PageRank loops gather the rank in BF16
+                                  (FP32 accumulation) until the residual falls
+                                  below the switch, then in FP32; 0 (default) off */
+} grb_option;
+
+/* Opaque handles. */
+typedef struct grb_context_s* grb_context;
+typedef struct grb_matrix_s* grb_matrix;
+typedef struct grb_vector_s* grb_vector;
+typedef struct grb_scalar_s* grb_scalar;
+
+/* Device allocator callbacks (for example, PyTorch's caching allocator).
+ * alloc returns a device pointer of at least `bytes` bytes usable on `stream`,
+ * or NULL; free releases it. */
+typedef void* (*grb_alloc_fn)(void* alloc_ctx, size_t bytes, void* stream);
+typedef void (*grb_free_fn)(void* alloc_ctx, void* ptr, void* stream);
+
+/* Counters for tests and benchmarks (grb_context_stats). */
+typedef struct grb_stats {
+    int64_t kernel_launches;    /* kernels launched by the library so far */
+    int64_t fused_groups;       /* fused kernels (more than one method each) */
+    int64_t unfused_nodes;      /* methods run one kernel each */
+    int64_t elided_vectors;     /* intermediate vectors never materialised */
+    int64_t persistent_loops;   /* grb_iterate_end calls run on the device */
+    int64_t replayed_loops;     /* grb_iterate_end calls replayed from the host */
+    int64_t device_bytes;       /* bytes currently held by the library */
+    int64_t cache_hits;         /* signature-table hits (§III-C) */
+} grb_stats;
+
+/* ------------------------------------------------------------ context */
+
+/* New context bound to a CUDA device stream (NULL = legacy default stream) of
+ * the current device.  alloc/free may be NULL (stream-ordered cudaMallocAsync
+ * is then used).  Errors: GRB_NULL_POINTER, GRB_INVALID_VALUE (bad mode),
+ * GRB_DEVICE_ERROR (no usable GPU). */
+grb_info grb_context_new(grb_context* ctx, grb_mode mode, void* cuda_stream,
+                         grb_alloc_fn alloc, grb_free_fn free_fn, void* alloc_ctx);
+grb_info grb_context_set(grb_context ctx, grb_option opt, int64_t value);
+grb_info grb_context_stats(grb_context ctx, grb_stats* out);
+/* Runs every pending method of the context and synchronises its stream. */
+grb_info grb_context_wait(grb_context ctx);
+
+/* ------------------------------------------------------------- matrix */
+
+/* Build a CSR matrix from a COO edge list (§IV: the PageRank listing takes
+ * A^T as input; 32-bit indices).  With GRB_BUILD_TRANSPOSE, row i of the
+ * stored matrix lists the sources j of the edges j -> i, ascending; otherwise
+ * row j lists the destinations.  vals == NULL stores a pattern-only, iso-1
+ * matrix (no value array; §III-C iso-valued objects).  The build sorts on the
+ * GPU, drops self loops / duplicates when asked, and is bit-exact integer
+ * work.  Errors: GRB_NULL_POINTER, GRB_INVALID_VALUE (sizes beyond 2^31-1,
+ * bad type), GRB_INDEX_OUT_OF_BOUNDS (an index outside [0, nrows/ncols)),
+ * GRB_OUT_OF_MEMORY. */
+grb_info grb_matrix_build_csr(grb_matrix* A, grb_context ctx, grb_type type, uint64_t nrows,
+                              uint64_t ncols, const int32_t* src, const int32_t* dst,
+                              const void* vals, uint64_t nedges, uint32_t flags);
+grb_info grb_matrix_nvals(uint64_t* nvals, grb_matrix A);
+grb_info grb_matrix_nrows(uint64_t* n, grb_matrix A);
+/* Copy the CSR arrays out (row_ptr: nrows+1 int32, col_idx: nvals int32,
+ * vals: nvals of the matrix type or NULL).  out_is_device selects device or
+ * host destination pointers. */
+grb_info grb_matrix_export_csr(grb_matrix A, int32_t* row_ptr, int32_t* col_idx, void* vals,
+                               int out_is_device);
+/* deg(j) = number of stored entries in column j of A (for A^T: the out-degree
+ * of vertex j in the graph; §IV's out_degree).  deg must be an INT32 vector
+ * of length ncols; vertices of degree 0 get no entry (GraphBLAS reduce
+ * semantics). */
+grb_info grb_matrix_col_degree(grb_vector deg, grb_matrix A);
+
+/* ------------------------------------------------------------- vector */
+
+/* New vector with no entries (§III-A GrBVector{T,I}(n)). */
+grb_info grb_vector_new(grb_vector* v, grb_context ctx, grb_type type, uint64_t n);
+/* Make v an iso-valued full vector: every entry equals *value (a double
+ * rounded to v's type).  Stores no array (§III-A GrBVector(n, v)). */
+grb_info grb_vector_fill(grb_vector v, double value);
+/* Replace v's content by the given entries (idx ascending, distinct;
+ * host or device pointers).  vals are doubles rounded to v's type. */
+grb_info grb_vector_build(grb_vector v, const int32_t* idx, const double* vals, uint64_t nvals,
+                          int ptrs_on_device);
+/* dst takes src's current value (O(1): the two share one immutable version;
+ * this is the `t = r` of the §IV listing). */
+grb_info grb_vector_copy(grb_vector dst, grb_vector src);
+grb_info grb_vector_size(uint64_t* n, grb_vector v);
+/* Number of entries; forces the vector's pending work. */
+grb_info grb_vector_nvals(uint64_t* nvals, grb_vector v);
+/* Copy the vector out as a dense array of its type (absent entries -> 0) and
+ * an optional uint8 presence array.  Forces pending work. */
+grb_info grb_vector_extract_dense(grb_vector v, void* values, uint8_t* present, int out_is_device);
+
+/* ------------------------------------------------------------- scalar */
+
+grb_info grb_scalar_new(grb_scalar* s, grb_context ctx, grb_type type);
+grb_info grb_scalar_set(grb_scalar s, double value);
+/* Read the value (forces pending work; §III footnote: a scalar is
+ * materialised before it is read).  GRB_NO_VALUE if the scalar is empty. */
+grb_info grb_scalar_get(grb_scalar s, double* value);
+/* out = op(in, k) on a (possibly pending) scalar. */
+grb_info grb_scalar_apply_bind2nd(grb_scalar out, grb_binop op, grb_scalar in, double k);
+
+/* ------------------------------------------------------------ methods
+ * All take the GraphBLAS write step: w<mask> accum= T, where `mask` may be
+ * NULL (all true), `accum` may be NULL (no accumulation), and `desc` holds
+ * REPLACE / STRUCTURE / COMPLEMENT.  Arithmetic runs in w's type (FP32 for
+ * BF16); inputs are converted to it. */
+
+/* w = op(u) on each entry of u (§III-B VectorApply). */
+grb_info grb_apply(grb_vector w, grb_vector mask, const grb_binop* accum, grb_unop op,
+                   grb_vector u, grb_desc desc);
+/* w = op(u, s) with the constant s bound as the second argument. */
+grb_info grb_apply_bind2nd(grb_vector w, grb_vector mask, const grb_binop* accum, grb_binop op,
+                           grb_vector u, double s, grb_desc desc);
+/* Same with a (possibly pending) scalar object as the bound argument. */
+grb_info grb_apply_bind2nd_scalar(grb_vector w, grb_vector mask, const grb_binop* accum,
+                                  grb_binop op, grb_vector u, grb_scalar s, grb_desc desc);
+/* w(i) = s for every index i (GrB_assign of a scalar to all indices); s may
+ * be pending. */
+grb_info grb_assign_scalar(grb_vector w, grb_vector mask, const grb_binop* accum, grb_scalar s,
+                           grb_desc desc);
+/* w = A (+.x) u over a semiring (§III-A MxV): row i gets an entry iff some
+ * A(i,j) meets an entry u(j). */
+grb_info grb_mxv(grb_vector w, grb_vector mask, const grb_binop* accum, grb_semiring s,
+                 grb_matrix A, grb_vector u, grb_desc desc);
+/* Union of index sets; op where both present (§III-D element-wise addition). */
+grb_info grb_ewise_add(grb_vector w, grb_vector mask, const grb_binop* accum, grb_binop op,
+                       grb_vector u, grb_vector v, grb_desc desc);
+/* Intersection of index sets (§III-D element-wise multiplication). */
+grb_info grb_ewise_mult(grb_vector w, grb_vector mask, const grb_binop* accum, grb_binop op,
+                        grb_vector u, grb_vector v, grb_desc desc);
+/* s accum= fold of the monoid over u's entries (identity when u is empty).
+ * Accumulation runs in FP64 and rounds once to s's type. */
+grb_info grb_reduce(grb_scalar s, const grb_binop* accum, grb_monoid m, grb_vector u, grb_desc desc);
+
+/* ------------------------------------------------------ materialisation */
+
+/* Complete the pending work that `obj` (a vector, scalar or matrix handle)
+ * depends on, fusing it (§II wait; §III-B materialize), and synchronise. */
+grb_info grb_wait(void* obj, grb_wait_mode mode);
+
+/* Loop capture (an extension that keeps nonblocking semantics).  Calls made
+ * between grb_iterate_begin and grb_iterate_end are recorded as one loop body
+ * instead of being run.  grb_iterate_end then executes
+ *     while (iters < itermax && value(cond) > tol) { body; iters++; }
+ * -- the loop test of the §IV listing, tested before each body.  When the
+ * body matches the fused PageRank iteration the whole loop runs on the GPU
+ * (one persistent kernel, or one fused kernel per iteration in a CUDA graph);
+ * otherwise the body is replayed through the normal planner each iteration.
+ * Every handle ends with the value the plain loop would give it. */
+grb_info grb_iterate_begin(grb_context ctx);
+grb_info grb_iterate_end(grb_context ctx, grb_scalar cond, double tol, int64_t itermax,
+                         int64_t* iters);
+
+/* Residual history of the last loop grb_iterate_end ran on the device:
+ * hist[k] = the loop condition's value after body k, for k < *n (at most
+ * cap written).  *mixed_phase (optional) is 1 when a mixed-precision loop
+ * switched to the FP32 gather, 0 when it did not, -1 for other loops. */
+grb_info grb_iterate_history(grb_context ctx, double* hist, int64_t cap, int64_t* n, int32_t* mixed_phase);
+
+/* -------------------------------------------------------------- misc */
+
+/* Release any handle (sets *obj to NULL).  Pending work that other objects
+ * still need is kept. */
+grb_info grb_free(void** obj);
+/* Last error message of a handle ("" if none). */
+const char* grb_error(void* obj);
+/* Self-test of the bounded device-side wait: launches a grid-barrier kernel
+ * in which one arrival never comes, with the given spin limit, and returns
+ * GRB_DEVICE_TIMEOUT once every block gave up (the GPU context stays
+ * usable).  Used by the failure-detection test. */
+grb_info grb_selftest_wait_timeout(grb_context ctx, int64_t spin_limit);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRB_H */

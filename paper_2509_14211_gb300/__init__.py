@@ -1,0 +1,418 @@
+"""Python binding of libgrb.so, the GB300 nonblocking-GraphBLAS library.
+
+Argument marshalling only: every function below calls the C entry point of
+the same name declared in include/grb.h, and every step of the computation
+runs in the library's CUDA kernels.  Importing the package loads libgrb.so
+and raises if it has not been built (``python -c "import __graft_entry__ as
+g; g.build()"``); there is no CPU fallback.
+
+Handles are plain integers (the C pointers).  Host arrays are numpy arrays;
+device arrays may be passed as torch CUDA tensors where a call accepts device
+pointers.  Errors raise GrbError carrying the grb_info code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [n for n in dir() if n.startswith("grb_") or n.startswith("GRB_")]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgrb.so")
+
+# ---------------------------------------------------------------- constants
+GRB_SUCCESS, GRB_NO_VALUE = 0, 1
+GRB_NULL_POINTER, GRB_INVALID_VALUE, GRB_INVALID_INDEX = -1, -2, -3
+GRB_DOMAIN_MISMATCH, GRB_DIMENSION_MISMATCH, GRB_UNINITIALIZED_OBJECT = -4, -5, -6
+GRB_NOT_IMPLEMENTED, GRB_INVALID_OBJECT = -7, -8
+GRB_OUT_OF_MEMORY, GRB_INDEX_OUT_OF_BOUNDS, GRB_DEVICE_ERROR = -101, -102, -103
+GRB_DEVICE_TIMEOUT, GRB_PANIC = -104, -105
+
+GRB_BLOCKING, GRB_NONBLOCKING = 0, 1
+GRB_INT32, GRB_FP32, GRB_FP64, GRB_BF16 = 1, 2, 3, 4
+(GRB_FIRST, GRB_SECOND, GRB_PLUS, GRB_MINUS, GRB_TIMES, GRB_DIV, GRB_MAX, GRB_MIN,
+ GRB_ABS_DIFF, GRB_MAX_DIV_BY) = range(1, 11)
+GRB_IDENTITY, GRB_ABS, GRB_AINV, GRB_MINV = 1, 2, 3, 4
+GRB_MONOID_PLUS, GRB_MONOID_MAX, GRB_MONOID_MIN, GRB_MONOID_TIMES = 1, 2, 3, 4
+(GRB_PLUS_TIMES, GRB_PLUS_SECOND, GRB_PLUS_FIRST, GRB_MAX_TIMES, GRB_MIN_PLUS,
+ GRB_MAX_SECOND) = range(1, 7)
+GRB_DESC_DEFAULT, GRB_DESC_REPLACE, GRB_DESC_STRUCTURE, GRB_DESC_COMPLEMENT = 0, 1, 2, 4
+GRB_BUILD_TRANSPOSE, GRB_BUILD_DROP_SELF, GRB_BUILD_DEDUP, GRB_BUILD_DEVICE_PTRS = 1, 2, 4, 8
+GRB_WAIT_COMPLETE, GRB_WAIT_MATERIALIZE = 0, 1
+GRB_OPT_FUSION, GRB_OPT_PERSISTENT, GRB_OPT_SPIN_LIMIT, GRB_OPT_MIXED_SWITCH, GRB_OPT_MIXED = 1, 2, 3, 4, 5
+
+NP_TYPES = {GRB_INT32: np.int32, GRB_FP32: np.float32, GRB_FP64: np.float64, GRB_BF16: np.uint16}
+
+
+class GrbError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str = ""):
+        super().__init__(f"{where} failed with grb_info {code}" + (f": {msg}" if msg else ""))
+        self.code = code
+
+
+class grb_binop(ctypes.Structure):
+    _fields_ = [("opcode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("k", ctypes.c_double)]
+
+
+class grb_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("kernel_launches", "fused_groups", "unfused_nodes",
+                                              "elided_vectors", "persistent_loops", "replayed_loops",
+                                              "device_bytes", "cache_hits")]
+
+
+def binop(code: int, k: float = 0.0) -> grb_binop:
+    return grb_binop(int(code), 0, float(k))
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+# ---------------------------------------------------------------- loading
+_lock = threading.Lock()
+_lib = None
+_keep = {}   # allocator callbacks per context (must outlive the context)
+
+
+def _declare(lib):
+    V, I, U64, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    B = grb_binop
+    sig = {
+        "grb_context_new": [P(V), I, V, ALLOC_FN, FREE_FN, V],
+        "grb_context_set": [V, I, I64],
+        "grb_context_stats": [V, P(grb_stats)],
+        "grb_context_wait": [V],
+        "grb_matrix_build_csr": [P(V), V, I, U64, U64, V, V, V, U64, ctypes.c_uint32],
+        "grb_matrix_nvals": [P(U64), V],
+        "grb_matrix_nrows": [P(U64), V],
+        "grb_matrix_export_csr": [V, V, V, V, I],
+        "grb_matrix_col_degree": [V, V],
+        "grb_vector_new": [P(V), V, I, U64],
+        "grb_vector_fill": [V, D],
+        "grb_vector_build": [V, V, V, U64, I],
+        "grb_vector_copy": [V, V],
+        "grb_vector_size": [P(U64), V],
+        "grb_vector_nvals": [P(U64), V],
+        "grb_vector_extract_dense": [V, V, V, I],
+        "grb_scalar_new": [P(V), V, I],
+        "grb_scalar_set": [V, D],
+        "grb_scalar_get": [V, P(D)],
+        "grb_scalar_apply_bind2nd": [V, B, V, D],
+        "grb_apply": [V, V, P(B), I, V, ctypes.c_uint32],
+        "grb_apply_bind2nd": [V, V, P(B), B, V, D, ctypes.c_uint32],
+        "grb_apply_bind2nd_scalar": [V, V, P(B), B, V, V, ctypes.c_uint32],
+        "grb_assign_scalar": [V, V, P(B), V, ctypes.c_uint32],
+        "grb_mxv": [V, V, P(B), I, V, V, ctypes.c_uint32],
+        "grb_ewise_add": [V, V, P(B), B, V, V, ctypes.c_uint32],
+        "grb_ewise_mult": [V, V, P(B), B, V, V, ctypes.c_uint32],
+        "grb_reduce": [V, P(B), I, V, ctypes.c_uint32],
+        "grb_wait": [V, I],
+        "grb_iterate_begin": [V],
+        "grb_iterate_end": [V, V, D, I64, P(I64)],
+        "grb_iterate_history": [V, P(D), I64, P(I64), P(ctypes.c_int32)],
+        "grb_free": [P(V)],
+        "grb_error": [V],
+        "grb_selftest_wait_timeout": [V, I64],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "grb_error" else ctypes.c_int
+
+
+def load():
+    """Load libgrb.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                                  "(__graft_entry__.build()); there is no CPU fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def symbols():
+    """Names of the entry points the binding declares (all of include/grb.h)."""
+    lib = load()
+    return [n for n in ("grb_context_new", "grb_context_set", "grb_context_stats", "grb_context_wait",
+                        "grb_matrix_build_csr", "grb_matrix_nvals", "grb_matrix_nrows", "grb_matrix_export_csr",
+                        "grb_matrix_col_degree", "grb_vector_new", "grb_vector_fill", "grb_vector_build",
+                        "grb_vector_copy", "grb_vector_size", "grb_vector_nvals", "grb_vector_extract_dense",
+                        "grb_scalar_new", "grb_scalar_set", "grb_scalar_get", "grb_scalar_apply_bind2nd",
+                        "grb_apply", "grb_apply_bind2nd", "grb_apply_bind2nd_scalar", "grb_assign_scalar",
+                        "grb_mxv", "grb_ewise_add", "grb_ewise_mult", "grb_reduce", "grb_wait",
+                        "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
+                        "grb_selftest_wait_timeout") if hasattr(lib, n)]
+
+
+def _check(rc: int, where: str, obj=None) -> int:
+    if rc < 0:
+        msg = ""
+        if obj:
+            try:
+                msg = (load().grb_error(obj) or b"").decode()
+            except Exception:
+                msg = ""
+        raise GrbError(rc, where, msg)
+    return rc
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None for None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _acc(accum):
+    return None if accum is None else ctypes.byref(accum)
+
+
+# ---------------------------------------------------------------- context
+def grb_context_new(mode: int = GRB_NONBLOCKING, stream=None, torch_allocator: bool = True) -> int:
+    """New context on the current CUDA device.  `stream` is a torch CUDA
+    stream (default: torch's current stream).  With torch_allocator, device
+    memory comes from torch's caching allocator."""
+    import torch
+    lib = load()
+    if not torch.cuda.is_available():
+        raise GrbError(GRB_DEVICE_ERROR, "grb_context_new", "no CUDA device")
+    dev = torch.cuda.current_device()
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    handle = ctypes.c_void_p(st.cuda_stream)
+    if torch_allocator:
+        def _alloc(_ctx, nbytes, stream_ptr):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream_ptr or 0))
+            except Exception:
+                return None
+
+        def _free(_ctx, ptr, _stream):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+        fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    else:
+        fa, ff = ALLOC_FN(), FREE_FN()
+    out = ctypes.c_void_p()
+    _check(lib.grb_context_new(ctypes.byref(out), int(mode), handle, fa, ff, None), "grb_context_new")
+    _keep[out.value] = (fa, ff, st)
+    return out.value
+
+
+def grb_context_set(ctx: int, opt: int, value: int) -> None:
+    _check(load().grb_context_set(ctx, int(opt), int(value)), "grb_context_set", ctx)
+
+
+def grb_context_stats(ctx: int) -> dict:
+    s = grb_stats()
+    _check(load().grb_context_stats(ctx, ctypes.byref(s)), "grb_context_stats", ctx)
+    return {n: getattr(s, n) for n, _ in grb_stats._fields_}
+
+
+def grb_context_wait(ctx: int) -> None:
+    _check(load().grb_context_wait(ctx), "grb_context_wait", ctx)
+
+
+# ----------------------------------------------------------------- matrix
+def grb_matrix_build_csr(ctx: int, type_: int, nrows: int, ncols: int, src, dst, vals=None,
+                         flags: int = GRB_BUILD_TRANSPOSE | GRB_BUILD_DROP_SELF | GRB_BUILD_DEDUP) -> int:
+    """CSR from COO.  src/dst: int32 numpy arrays (host) or int32 torch CUDA
+    tensors (device; GRB_BUILD_DEVICE_PTRS is then added)."""
+    if _is_device(src):
+        flags |= GRB_BUILD_DEVICE_PTRS
+    else:
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        if vals is not None:
+            vals = np.ascontiguousarray(vals, dtype=NP_TYPES[type_])
+    out = ctypes.c_void_p()
+    _check(load().grb_matrix_build_csr(ctypes.byref(out), ctx, int(type_), int(nrows), int(ncols), _ptr(src),
+                                       _ptr(dst), _ptr(vals), len(src), int(flags)), "grb_matrix_build_csr", ctx)
+    return out.value
+
+
+def grb_matrix_nvals(A: int) -> int:
+    n = ctypes.c_uint64()
+    _check(load().grb_matrix_nvals(ctypes.byref(n), A), "grb_matrix_nvals")
+    return n.value
+
+
+def grb_matrix_nrows(A: int) -> int:
+    n = ctypes.c_uint64()
+    _check(load().grb_matrix_nrows(ctypes.byref(n), A), "grb_matrix_nrows")
+    return n.value
+
+
+def grb_matrix_export_csr(A: int):
+    """(row_ptr, col_idx) as int32 numpy arrays."""
+    n, nnz = grb_matrix_nrows(A), grb_matrix_nvals(A)
+    rp = np.empty(n + 1, dtype=np.int32)
+    ci = np.empty(max(nnz, 1), dtype=np.int32)
+    _check(load().grb_matrix_export_csr(A, _ptr(rp), _ptr(ci), None, 0), "grb_matrix_export_csr", A)
+    return rp, ci[:nnz]
+
+
+def grb_matrix_col_degree(deg: int, A: int) -> None:
+    _check(load().grb_matrix_col_degree(deg, A), "grb_matrix_col_degree", deg)
+
+
+# ----------------------------------------------------------------- vector
+def grb_vector_new(ctx: int, type_: int, n: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().grb_vector_new(ctypes.byref(out), ctx, int(type_), int(n)), "grb_vector_new", ctx)
+    return out.value
+
+
+def grb_vector_fill(v: int, value: float) -> None:
+    _check(load().grb_vector_fill(v, float(value)), "grb_vector_fill", v)
+
+
+def grb_vector_build(v: int, idx, vals) -> None:
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    _check(load().grb_vector_build(v, _ptr(idx), _ptr(vals), len(idx), 0), "grb_vector_build", v)
+
+
+def grb_vector_copy(dst: int, src: int) -> None:
+    _check(load().grb_vector_copy(dst, src), "grb_vector_copy", dst)
+
+
+def grb_vector_size(v: int) -> int:
+    n = ctypes.c_uint64()
+    _check(load().grb_vector_size(ctypes.byref(n), v), "grb_vector_size", v)
+    return n.value
+
+
+def grb_vector_nvals(v: int) -> int:
+    n = ctypes.c_uint64()
+    _check(load().grb_vector_nvals(ctypes.byref(n), v), "grb_vector_nvals", v)
+    return n.value
+
+
+def grb_vector_extract_dense(v: int, type_: int, out=None, present: bool = True):
+    """Values (numpy array of the vector's type, absent -> 0) and a uint8
+    presence array.  With `out` a torch CUDA tensor the values are written to
+    the device instead and (out, None) is returned."""
+    n = grb_vector_size(v)
+    if out is not None and _is_device(out):
+        _check(load().grb_vector_extract_dense(v, _ptr(out), None, 1), "grb_vector_extract_dense", v)
+        return out, None
+    vals = np.empty(n, dtype=NP_TYPES[type_])
+    pres = np.empty(n, dtype=np.uint8) if present else None
+    _check(load().grb_vector_extract_dense(v, _ptr(vals), _ptr(pres), 0), "grb_vector_extract_dense", v)
+    return vals, pres
+
+
+# ----------------------------------------------------------------- scalar
+def grb_scalar_new(ctx: int, type_: int = GRB_FP64) -> int:
+    out = ctypes.c_void_p()
+    _check(load().grb_scalar_new(ctypes.byref(out), ctx, int(type_)), "grb_scalar_new", ctx)
+    return out.value
+
+
+def grb_scalar_set(s: int, value: float) -> None:
+    _check(load().grb_scalar_set(s, float(value)), "grb_scalar_set", s)
+
+
+def grb_scalar_get(s: int):
+    """The scalar's value, or None when it holds no value."""
+    x = ctypes.c_double()
+    rc = _check(load().grb_scalar_get(s, ctypes.byref(x)), "grb_scalar_get", s)
+    return None if rc == GRB_NO_VALUE else x.value
+
+
+def grb_scalar_apply_bind2nd(out: int, op: grb_binop, s: int, k: float) -> None:
+    _check(load().grb_scalar_apply_bind2nd(out, op, s, float(k)), "grb_scalar_apply_bind2nd", out)
+
+
+# ---------------------------------------------------------------- methods
+def grb_apply(w, mask, accum, op, u, desc=0):
+    _check(load().grb_apply(w, mask, _acc(accum), int(op), u, int(desc)), "grb_apply", w)
+
+
+def grb_apply_bind2nd(w, mask, accum, op, u, s, desc=0):
+    _check(load().grb_apply_bind2nd(w, mask, _acc(accum), op, u, float(s), int(desc)), "grb_apply_bind2nd", w)
+
+
+def grb_apply_bind2nd_scalar(w, mask, accum, op, u, s, desc=0):
+    _check(load().grb_apply_bind2nd_scalar(w, mask, _acc(accum), op, u, s, int(desc)), "grb_apply_bind2nd_scalar", w)
+
+
+def grb_assign_scalar(w, mask, accum, s, desc=0):
+    _check(load().grb_assign_scalar(w, mask, _acc(accum), s, int(desc)), "grb_assign_scalar", w)
+
+
+def grb_mxv(w, mask, accum, semiring, A, u, desc=0):
+    _check(load().grb_mxv(w, mask, _acc(accum), int(semiring), A, u, int(desc)), "grb_mxv", w)
+
+
+def grb_ewise_add(w, mask, accum, op, u, v, desc=0):
+    _check(load().grb_ewise_add(w, mask, _acc(accum), op, u, v, int(desc)), "grb_ewise_add", w)
+
+
+def grb_ewise_mult(w, mask, accum, op, u, v, desc=0):
+    _check(load().grb_ewise_mult(w, mask, _acc(accum), op, u, v, int(desc)), "grb_ewise_mult", w)
+
+
+def grb_reduce(s, accum, monoid, u, desc=0):
+    _check(load().grb_reduce(s, _acc(accum), int(monoid), u, int(desc)), "grb_reduce", s)
+
+
+def grb_wait(obj, mode=GRB_WAIT_MATERIALIZE):
+    _check(load().grb_wait(obj, int(mode)), "grb_wait", obj)
+
+
+def grb_iterate_begin(ctx):
+    _check(load().grb_iterate_begin(ctx), "grb_iterate_begin", ctx)
+
+
+def grb_iterate_end(ctx, cond, tol, itermax) -> int:
+    it = ctypes.c_int64()
+    _check(load().grb_iterate_end(ctx, cond, float(tol), int(itermax), ctypes.byref(it)), "grb_iterate_end", ctx)
+    return it.value
+
+
+def grb_iterate_history(ctx):
+    """(residual history of the last device loop, mixed-precision phase)."""
+    n = ctypes.c_int64()
+    ph = ctypes.c_int32()
+    _check(load().grb_iterate_history(ctx, None, 0, ctypes.byref(n), ctypes.byref(ph)), "grb_iterate_history", ctx)
+    h = np.empty(max(n.value, 1), dtype=np.float64)
+    _check(load().grb_iterate_history(ctx, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                                      ctypes.byref(n), ctypes.byref(ph)), "grb_iterate_history", ctx)
+    return h[:n.value], ph.value
+
+
+def grb_free(obj) -> None:
+    if not obj:
+        return
+    p = ctypes.c_void_p(obj)
+    _check(load().grb_free(ctypes.byref(p)), "grb_free")
+    _keep.pop(obj, None)
+
+
+def grb_error(obj) -> str:
+    return (load().grb_error(obj) or b"").decode()
+
+
+def grb_selftest_wait_timeout(ctx, spin_limit: int) -> int:
+    """Returns the grb_info code (GRB_DEVICE_TIMEOUT expected)."""
+    return load().grb_selftest_wait_timeout(ctx, int(spin_limit))
+
+
+__all__ = [n for n in list(globals()) if n.startswith("grb_") or n.startswith("GRB_")] + \
+    ["GrbError", "binop", "load", "symbols", "NP_TYPES"]

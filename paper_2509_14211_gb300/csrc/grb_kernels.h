@@ -1,0 +1,189 @@
+// Host-callable launchers of the CUDA kernels and the plain-data structs they
+// take.  Nothing here knows about handles or the DAG; grb_core.h builds these
+// descriptors from materialised versions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace grb {
+
+enum class Fmt : int32_t { EMPTY = 0, ISO = 1, FULL = 2, BITMAP = 3 };
+
+// Read-only vector operand.  ISO: every entry equals `iso`; FULL: `vals`
+// holds n values; BITMAP: `vals` + `present` (uint8 per entry).
+struct VIn {
+    const void* vals = nullptr;
+    const uint8_t* present = nullptr;
+    double iso = 0.0;
+    const double* iso_slot = nullptr;  // ISO value held in device memory (pending scalar)
+    int32_t type = 2;                  // grb_type
+    int32_t fmt = 0;                   // Fmt
+};
+
+// Output vector: values of `type`; `present` written unless `full`.
+struct VOut {
+    void* vals = nullptr;
+    uint8_t* present = nullptr;
+    int32_t type = 2;
+    int32_t full = 1;
+};
+
+// Scalar operand: device slot (a double) when non-null, else the host value.
+struct SIn {
+    const double* slot = nullptr;
+    double host = 0.0;
+};
+
+struct OpSpec {
+    int32_t code = 0;  // grb_opcode
+    double k = 0.0;
+};
+
+// Scalar post-processing chain: x = op_i(x, c_i), applied in order.
+struct SChain {
+    int32_t n = 0;
+    OpSpec ops[6];
+    double c[6] = {0, 0, 0, 0, 0, 0};
+    int32_t rtype[6] = {3, 3, 3, 3, 3, 3};  // type each step rounds to
+};
+
+enum EwKind : int32_t { EW_APPLY = 1, EW_APPLY_B2 = 2, EW_ASSIGN = 3, EW_EADD = 4, EW_EMULT = 5, EW_COPY = 6 };
+
+// Element-wise method T(i) (before the write step).
+struct EwSpec {
+    int32_t kind = EW_COPY;
+    OpSpec op;
+    int32_t unop = 0;
+    int32_t ctype = 2;   // type the op computes and rounds in (output's type)
+    VIn u, v;
+    SIn s;
+};
+
+// GraphBLAS write step: w<mask> accum= T.
+struct WriteSpec {
+    VIn mask;
+    int32_t use_mask = 0, structural = 0, complement = 0, replace = 0;
+    int32_t has_accum = 0;
+    OpSpec accum;
+    VIn w_old;
+};
+
+// Merge-path tile plan of a CSR matrix.
+constexpr int PR_BLOCK = 256;
+constexpr int PR_ITEMS = 8;
+constexpr int PR_TILE = PR_BLOCK * PR_ITEMS;
+
+struct SyncWords {
+    uint32_t launch;     // last epoch used by the look-back flags
+    uint32_t bar_count;  // grid barrier arrivals
+    uint32_t bar_gen;    // grid barrier generation
+    uint32_t done;       // last-block-done counter
+    uint32_t stop;       // latched "converged" flag of per-iteration launches
+    uint32_t pad[3];
+};
+
+enum GatherMode : int32_t { G_W = 0, G_TD = 1, G_ISO = 2 };
+
+// Fused row-gather kernel over the rows of a CSR matrix (merge-path tiles):
+//   s_i   = sum over j in row i of g(j),  g = w[j] | t[j]/d[j] | g_iso
+//   out_i = base_i + s_i (row non-empty) | base_i (row empty)   when has_base
+//         = s_i, present iff row non-empty                        otherwise
+// plus optional epilogue outputs: w_next_i = out_i / dd_i, the residual
+// sum |r_old_i - out_i| and the dangling mass sum over sink rows of out_i.
+struct PrParams {
+    // matrix and plan
+    const int32_t* row_ptr = nullptr;
+    const int32_t* col_idx = nullptr;
+    int32_t nrows = 0, nnz = 0;
+    const int32_t* tile_i = nullptr;
+    const int32_t* tile_k = nullptr;
+    int32_t ntiles = 0;
+    double* agg = nullptr;
+    uint32_t* flag = nullptr;
+    double* part = nullptr;      // [2][grid][2]
+    SyncWords* sync = nullptr;
+    int32_t* status = nullptr;
+    int64_t spin_limit = 1 << 24;
+    // gather
+    int32_t gmode = G_W;
+    const void* w = nullptr;     // G_W gather vector (gather type)
+    const void* t = nullptr;     // G_TD numerator (rank type)
+    const void* d = nullptr;     // G_TD divisor (rank type)
+    double g_iso = 0.0;
+    // base (accumulated output / teleport)
+    int32_t has_base = 0;
+    VIn base;
+    // outputs
+    VOut out;
+    void* w_next = nullptr;      // gather type
+    const void* dd = nullptr;    // divisor of w_next (rank type, full)
+    const uint32_t* sinkbits = nullptr;
+    const void* r_old = nullptr; // residual reference (rank type, full)
+    int32_t want_resid = 0, want_dang = 0;
+    double* resid_slot = nullptr;
+    int32_t resid_type = 3;
+    double* dang_slot = nullptr;
+    double* tele_slot = nullptr; // chain(dangling mass)
+    SChain chain;
+    // persistent / iterated execution
+    int32_t iters = 1;           // persistent: maximum number of bodies
+    int32_t iter_index = 0;      // per-iteration launch: index of this body
+    double tol = -1.0;
+    double* hist = nullptr;      // residual history (itermax doubles)
+    int64_t* iters_done = nullptr;
+    const void* r0 = nullptr;    // persistent: input of body 0
+    void* rbuf[2] = {nullptr, nullptr};
+    void* wbuf[2] = {nullptr, nullptr};
+    double rdiff0 = 1.0;         // value of the loop condition before body 0
+    int32_t tele_from_slot = 0;  // base is the scalar tele_slot (uniform dangling)
+    // mixed precision (BF16 gather until the residual drops below mixed_switch)
+    int32_t mixed = 0;
+    double mixed_switch = 1e-3;
+    void* wbuf32[2] = {nullptr, nullptr};
+    int32_t* mixed_phase = nullptr;  // 0 = BF16 gather, 1 = FP32 gather
+};
+
+// --------------------------------------------------------------- launchers
+cudaError_t launch_ewise(cudaStream_t st, int64_t n, const EwSpec& e, const WriteSpec& w, VOut out);
+cudaError_t launch_ew_reduce(cudaStream_t st, int64_t n, const EwSpec& e, int32_t monoid, int32_t has_accum,
+                             OpSpec accum, SIn s_old, const SChain& chain, int32_t out_type, double* out_slot,
+                             double* scratch, uint32_t* counter, int grid);
+cudaError_t launch_scalar_chain(cudaStream_t st, SIn in, const SChain& chain, int32_t out_type, double* out_slot);
+cudaError_t launch_count_present(cudaStream_t st, int64_t n, const uint8_t* present, unsigned long long* out);
+cudaError_t launch_to_dense(cudaStream_t st, int64_t n, VIn v, void* out_vals, uint8_t* out_present);
+cudaError_t launch_build_sparse(cudaStream_t st, int64_t n, const int32_t* idx, const double* vals, int64_t nvals,
+                                int32_t type, void* out_vals, uint8_t* out_present, int32_t* status);
+cudaError_t launch_sinkbits(cudaStream_t st, int64_t n, VIn v, uint32_t* bits);
+cudaError_t launch_mxv_generic(cudaStream_t st, int64_t nrows, const int32_t* row_ptr, const int32_t* col_idx,
+                               const void* avals, int32_t a_type, double a_iso, VIn u, int32_t add_monoid,
+                               int32_t mul_op, VOut out);
+
+// CSR build: returns the deduplicated nnz through *nnz_out (synchronises).
+struct CsrBuildArgs {
+    int64_t nrows, ncols, nedges;
+    const int32_t* src;   // device
+    const int32_t* dst;   // device
+    const void* vals;     // device or null
+    int32_t val_type;
+    int32_t transpose, drop_self, dedup;
+};
+using AllocFn = void* (*)(void* ctx, size_t bytes);
+using FreeFn = void (*)(void* ctx, void* p, size_t bytes);
+cudaError_t csr_build(cudaStream_t st, const CsrBuildArgs& a, AllocFn af, FreeFn ff, void* actx,
+                      int32_t** row_ptr, int32_t** col_idx, void** vals_out, int64_t* nnz_out, int32_t* bad_index);
+cudaError_t launch_col_degree(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx,
+                              int32_t* deg, uint8_t* present);
+cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* row_ptr, unsigned long long* out);
+
+// Merge-path plan and the fused kernels.
+cudaError_t launch_tile_plan(cudaStream_t st, const int32_t* row_ptr, int32_t nrows, int32_t nnz, int64_t ntiles,
+                             int32_t* tile_i, int32_t* tile_k);
+// Resident CTAs per SM of the fused kernel for the given rank / gather types.
+int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent);
+cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,
+                      int persistent);
+cudaError_t launch_barrier_selftest(cudaStream_t st, SyncWords* sync, int32_t* status, int64_t spin_limit, int grid);
+
+}  // namespace grb

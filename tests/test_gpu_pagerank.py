@@ -1,0 +1,182 @@
+"""PageRank on the GPU through the C-ABI against the FP64 CPU oracle.
+
+Readings (the paper is silent on them): the FP64 and fixed-iteration cases
+compare with the oracle run for the same number of iterations as the GPU
+reports; FP64 must agree to max-abs 1e-12 per entry and FP32 to L1 1e-6.
+Execution paths compared: persistent device loop, CUDA-graph device loop,
+host loop with per-wait fusion, blocking mode (one kernel per method)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+D = 0.85
+
+
+@pytest.fixture(scope="module")
+def grb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2509_14211_gb300 as g
+
+    g.load()
+    return g
+
+
+def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, persistent=0, fusion=True,
+         mixed=False):
+    from paper_2509_14211_gb300.pagerank import pagerank
+
+    ctx = grb.grb_context_new(mode if mode is not None else grb.GRB_NONBLOCKING)
+    grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, persistent)
+    grb.grb_context_set(ctx, grb.GRB_OPT_FUSION, 1 if fusion else 0)
+    grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 1 if mixed else 0)
+    try:
+        r, it = pagerank(ctx, n, src, dst, damping=D, tol=tol, itermax=itermax, rank_type=rank_type,
+                         dangling=dangling, loop=loop)
+        stats = grb.grb_context_stats(ctx)
+        hist = grb.grb_iterate_history(ctx)
+    finally:
+        grb.grb_free(ctx)
+    return r, it, stats, hist
+
+
+@pytest.fixture(scope="module")
+def c0():
+    """R-MAT scale 10, edge factor 16, seed 0 (the small FP64 configuration)."""
+    n = 1 << 10
+    src, dst = graphgen.rmat_edges(10, 16, seed=0)
+    return n, src, dst
+
+
+PATHS = [("device", 1, True, "nb"), ("device", 2, True, "nb"), ("host", 0, True, "nb"),
+         ("host", 0, False, "nb"), ("host", 0, True, "blocking")]
+
+
+@pytest.mark.parametrize("loop,persistent,fusion,mode", PATHS)
+@pytest.mark.parametrize("dangling", ["uniform", "gap"])
+def test_fp64_rmat10_all_paths(grb, c0, loop, persistent, fusion, mode, dangling):
+    n, src, dst = c0
+    m = grb.GRB_BLOCKING if mode == "blocking" else grb.GRB_NONBLOCKING
+    r, it, stats, _ = _run(grb, n, src, dst, grb.GRB_FP64, dangling, loop, 1e-10, 100, m, persistent, fusion)
+    ref_conv, k_conv, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=1e-10, itermax=100, mode=dangling)
+    assert abs(it - k_conv) <= 1
+    ref, k, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=it, mode=dangling)
+    assert np.max(np.abs(r - ref)) <= 1e-12
+    if loop == "device":
+        assert stats["persistent_loops"] == 1
+    if mode == "blocking" or not fusion:
+        assert stats["fused_groups"] == 0
+    elif loop == "host":
+        assert stats["fused_groups"] >= it and stats["elided_vectors"] > 0
+
+
+@pytest.mark.parametrize("dangling", ["uniform", "gap"])
+def test_fp32_fixed_iterations_scale16(grb, dangling):
+    n = 1 << 16
+    src, dst = graphgen.rmat_edges(16, 16, seed=1)
+    ref, _, ref_hist = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=50, mode=dangling)
+    for persistent in (1, 2):
+        r, it, _, (hist, _) = _run(grb, n, src, dst, grb.GRB_FP32, dangling, "device", -1.0, 50,
+                                   persistent=persistent)
+        assert it == 50
+        assert np.sum(np.abs(r - ref)) <= 1e-6
+        # FP32 ranks put a noise floor of ~n * eps32 * mean(r) ~ 1e-8 under
+        # the L1 change between iterates
+        np.testing.assert_allclose(hist, ref_hist, rtol=1e-3, atol=1e-7)
+    r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP32, dangling, "host", -1.0, 50)
+    assert it == 50 and np.sum(np.abs(r - ref)) <= 1e-6
+
+
+def test_fp32_full_size_rmat22(grb):
+    """R-MAT scale 22 (4.19M vertices, 67M raw edges), FP32 ranks, FP64
+    residual, 50 fixed iterations: the benchmark configuration."""
+    n = 1 << 22
+    src, dst = graphgen.rmat_edges(22, 16, seed=1)
+    r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", -1.0, 50, persistent=1)
+    ref, k, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=50, mode="uniform")
+    assert it == 50 == k
+    assert np.sum(np.abs(r - ref)) <= 1e-6
+    assert abs(np.sum(r) - 1.0) < 1e-4 and np.all(r >= 0)
+
+
+def test_mixed_precision_refines_to_fp32(grb):
+    n = 1 << 15
+    src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
+    r, it, _, (hist, phase) = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", 1e-7, 200,
+                                   persistent=1, mixed=True)
+    assert phase == 1                      # switched to the FP32 gather
+    ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=1e-14, itermax=1000, mode="uniform")
+    assert np.sum(np.abs(r - ref)) <= 1e-6
+
+
+def test_deterministic_and_resumable(grb):
+    from paper_2509_14211_gb300.pagerank import PageRankProblem, build_graph
+
+    n = 1 << 14
+    src, dst = graphgen.rmat_edges(14, 16, seed=3)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    try:
+        AT = build_graph(ctx, n, src, dst)
+        P = PageRankProblem(ctx, AT, n, D, grb.GRB_FP32)
+        P.run(-1.0, 20)
+        a = P.rank().copy()
+        P.run(-1.0, 20)
+        b = P.rank().copy()
+        assert np.array_equal(a, b)                       # bit-reproducible
+        # checkpoint after 12 bodies, resume for 8 more
+        P.run(-1.0, 12)
+        ck = P.rank().copy()
+        grb.grb_vector_build(P.r, np.arange(n, dtype=np.int32), ck.astype(np.float64))
+        grb.grb_scalar_set(P.rdiff, 1.0)
+        grb.grb_iterate_begin(ctx)
+        P.body()
+        assert grb.grb_iterate_end(ctx, P.rdiff, -1.0, 8) == 8
+        np.testing.assert_allclose(P.rank(), a, rtol=0, atol=1e-9)
+        P.free()
+        grb.grb_free(AT)
+    finally:
+        grb.grb_free(ctx)
+
+
+@pytest.mark.parametrize("case", ["single_vertex", "edgeless", "hub", "ragged"])
+def test_edge_graphs(grb, case):
+    if case == "single_vertex":
+        n, src, dst = 1, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    elif case == "edgeless":
+        n, src, dst = 1000, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    elif case == "hub":      # one row of ~100k in-edges spans ~50 tiles
+        rng = np.random.default_rng(9)
+        n = 150000
+        src = rng.integers(0, n, 120000).astype(np.int32)
+        dst = np.where(rng.random(120000) < 0.8, 7, rng.integers(0, n, 120000)).astype(np.int32)
+    else:
+        rng = np.random.default_rng(10)
+        n = 12345
+        src = rng.integers(0, n, 40000).astype(np.int32)
+        dst = (rng.integers(0, n // 7, 40000) * 7).astype(np.int32)
+    for rank_type, tol_ok in ((grb.GRB_FP64, 1e-12), (grb.GRB_FP32, 1e-6)):
+        ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=15, mode="uniform")
+        for loop in ("device", "host"):
+            r, it, _, _ = _run(grb, n, src, dst, rank_type, "uniform", loop, -1.0, 15)
+            assert it == 15
+            err = np.max(np.abs(r - ref)) if rank_type == grb.GRB_FP64 else np.sum(np.abs(r - ref))
+            assert err <= tol_ok, (case, loop, err)
+
+
+def test_loop_kernel_counts(grb, c0):
+    """Fusion shows in the launch counts: the device loop launches one kernel
+    per loop, the host loop a few per iteration, blocking mode one per
+    method."""
+    n, src, dst = c0
+    _, it_d, sd, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", -1.0, 30, persistent=1)
+    _, it_h, sh, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "host", -1.0, 30)
+    _, it_b, sb, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "host", -1.0, 30, mode=grb.GRB_BLOCKING)
+    assert it_d == it_h == it_b == 30
+    assert sh["kernel_launches"] - sd["kernel_launches"] >= 2 * 30
+    assert sb["kernel_launches"] > sh["kernel_launches"]
+    assert sb["fused_groups"] == 0 and sh["fused_groups"] >= 30
