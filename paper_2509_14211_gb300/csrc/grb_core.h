@@ -93,8 +93,10 @@ struct Node {
 struct TilePlan {
     int64_t ntiles = 0;
     DevBuf tile_i, tile_k;     // merge-path coordinates of each tile start (ntiles+1)
-    DevBuf agg, flag;          // per-tile carry-out value (double) and epoch flag
-    int grid_pr = 0;           // resident CTAs of the fused kernels
+    DevBuf agg, first;         // per-tile carry of the open last row / partial of the first row
+    DevBuf fix;                // per-tile fixup descriptor (row of a split first row, first tile of it)
+    DevBuf longfix;            // tiles whose split first row spans more than PR_LONG tiles
+    int64_t nlong = 0;
     DevBuf part;               // 2 x grid_pr x 2 doubles (residual, dangling mass)
     DevBuf sync;               // device counters (SyncWords)
     std::vector<DevBuf> loop_bufs;
@@ -213,6 +215,8 @@ grb_info cuda_check(Ctx* c, cudaError_t e, const char* what);
 grb_info ensure_plan(Ctx* c, Matrix* A);
 grb_info ensure_sinkbits(Ctx* c, Version* sinks);
 grb_info read_status(Ctx* c);
+PrParams plan_params_of(Ctx* c, Matrix* A);
+int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent);
 double round_host(grb_type t, double x);
 double host_binop(int32_t code, double k, double x, double y);
 bool guaranteed_full(const Version* v);

@@ -136,24 +136,36 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
     if (A->plan) return GRB_SUCCESS;
     TilePlan* p = new TilePlan();
     const int64_t total = A->nrows + A->nnz;
-    p->ntiles = (total + PR_TILE - 1) / PR_TILE;
+    p->ntiles = (total + PR_WTILE - 1) / PR_WTILE;
     if (p->ntiles < 1) p->ntiles = 1;
     p->tile_i = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 1));
     p->tile_k = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 1));
     p->agg = buf_alloc(c, sizeof(double) * p->ntiles);
-    p->flag = buf_alloc(c, sizeof(uint32_t) * p->ntiles);
+    p->first = buf_alloc(c, sizeof(double) * p->ntiles);
+    p->fix = buf_alloc(c, sizeof(FixDesc) * p->ntiles);
+    p->longfix = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 1));
     p->part = buf_alloc(c, sizeof(double) * 2 * 2 * (size_t)c->sm_count * 8);
     p->sync = buf_alloc(c, sizeof(SyncWords));
     A->plan = p;
-    if (!p->tile_i.p || !p->tile_k.p || !p->agg.p || !p->flag.p || !p->part.p || !p->sync.p) return GRB_OUT_OF_MEMORY;
+    if (!p->tile_i.p || !p->tile_k.p || !p->agg.p || !p->first.p || !p->fix.p || !p->longfix.p || !p->part.p ||
+        !p->sync.p)
+        return GRB_OUT_OF_MEMORY;
+    int32_t* nlong_dev = (int32_t*)p->longfix.p + p->ntiles;
     grb_info st = cuda_check(c, launch_tile_plan(c->stream, (const int32_t*)A->row_ptr.p, (int32_t)A->nrows,
                                                  (int32_t)A->nnz, p->ntiles, (int32_t*)p->tile_i.p,
                                                  (int32_t*)p->tile_k.p), "tile plan");
+    if (!st)
+        st = cuda_check(c, launch_fix_plan(c->stream, (const int32_t*)A->row_ptr.p, p->ntiles,
+                                           (const int32_t*)p->tile_i.p, (const int32_t*)p->tile_k.p,
+                                           (FixDesc*)p->fix.p, (int32_t*)p->longfix.p, nlong_dev), "fixup plan");
     if (st) return st;
-    c->stats.kernel_launches++;
-    st = cuda_check(c, cudaMemsetAsync(p->flag.p, 0, sizeof(uint32_t) * p->ntiles, c->stream), "plan flags");
-    if (st) return st;
-    return cuda_check(c, cudaMemsetAsync(p->sync.p, 0, sizeof(SyncWords), c->stream), "plan sync");
+    c->stats.kernel_launches += 2;
+    int32_t nlong = 0;
+    st = cuda_check(c, cudaMemcpyAsync(&nlong, nlong_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "plan");
+    if (!st) st = cuda_check(c, cudaMemsetAsync(p->sync.p, 0, sizeof(SyncWords), c->stream), "plan sync");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "plan");
+    p->nlong = nlong;
+    return st;
 }
 
 grb_info ensure_sinkbits(Ctx* c, Version* s) {
@@ -175,7 +187,10 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
     p.tile_k = (const int32_t*)pl->tile_k.p;
     p.ntiles = (int32_t)pl->ntiles;
     p.agg = (double*)pl->agg.p;
-    p.flag = (uint32_t*)pl->flag.p;
+    p.first = (double*)pl->first.p;
+    p.fix = (const FixDesc*)pl->fix.p;
+    p.longfix = (const int32_t*)pl->longfix.p;
+    p.nlong = (int32_t)pl->nlong;
     p.part = (double*)pl->part.p;
     p.sync = (SyncWords*)pl->sync.p;
     p.status = (int32_t*)c->status.p;
@@ -183,10 +198,13 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
     return p;
 }
 
-static int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent) {
+PrParams plan_params_of(Ctx* c, Matrix* A) { return plan_params(c, A); }
+
+int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent) {
     int g = pr_blocks_per_sm(T, G, gmode, persistent) * c->sm_count;
     if (g > c->sm_count * 8) g = c->sm_count * 8;
-    if (g > A->plan->ntiles) g = (int)A->plan->ntiles;
+    const int64_t need = (A->plan->ntiles + PR_BLOCK / 32 - 1) / (PR_BLOCK / 32);   // one tile per warp at least
+    if (g > need) g = (int)need;
     return g < 1 ? 1 : g;
 }
 

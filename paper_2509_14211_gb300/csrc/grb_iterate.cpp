@@ -274,23 +274,7 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     int64_t* iters_done = (int64_t*)(sl + 0);
     if (!st) st = cuda_check(c, cudaMemsetAsync(slots.p, 0, sizeof(double) * 8, c->stream), "loop slots");
 
-    PrParams p;
-    {
-        TilePlan* pl = A->plan;
-        p.row_ptr = (const int32_t*)A->row_ptr.p;
-        p.col_idx = (const int32_t*)A->col_idx.p;
-        p.nrows = (int32_t)A->nrows;
-        p.nnz = (int32_t)A->nnz;
-        p.tile_i = (const int32_t*)pl->tile_i.p;
-        p.tile_k = (const int32_t*)pl->tile_k.p;
-        p.ntiles = (int32_t)pl->ntiles;
-        p.agg = (double*)pl->agg.p;
-        p.flag = (uint32_t*)pl->flag.p;
-        p.part = (double*)pl->part.p;
-        p.sync = (SyncWords*)pl->sync.p;
-        p.status = (int32_t*)c->status.p;
-        p.spin_limit = c->spin_limit;
-    }
+    PrParams p = plan_params_of(c, A);
     p.gmode = G_W;
     p.has_base = 1;
     if (lm.uniform) {
@@ -327,14 +311,13 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
 
     const int mode = (c->persistent == 2 && !mixed) ? 2 : 1;
     if (!st && mode == 1) {
-        const int grid = std::min(pr_blocks_per_sm(T, G, G_W, 1) * c->sm_count, c->sm_count * 8);
+        const int grid = pr_grid(c, A, T, G, G_W, 1);
         c->stats.kernel_launches++;
         st = cuda_check(c, launch_pr(c->stream, p, T, G, grid, 1), "persistent pagerank loop");
     } else if (!st) {
         // prologue (no bodies) + one fused kernel per body, as a CUDA graph
-        const int pgrid = std::min(pr_blocks_per_sm(T, G, G_W, 1) * c->sm_count, c->sm_count * 8);
-        int igrid = pr_blocks_per_sm(T, G, G_W, 0) * c->sm_count;
-        igrid = std::max(1, std::min<int>(igrid, std::min<int64_t>(c->sm_count * 8, A->plan->ntiles)));
+        const int pgrid = pr_grid(c, A, T, G, G_W, 1);
+        const int igrid = pr_grid(c, A, T, G, G_W, 0);
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         // capture on a private stream (the context's stream may be the

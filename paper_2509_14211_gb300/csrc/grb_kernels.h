@@ -70,18 +70,27 @@ struct WriteSpec {
     VIn w_old;
 };
 
-// Merge-path tile plan of a CSR matrix.
+// Merge-path tile plan of a CSR matrix: every warp takes tiles of
+// PR_WTILE merge items (row ends + nonzeros), PR_WITEMS per lane.
 constexpr int PR_BLOCK = 256;
-constexpr int PR_ITEMS = 8;
-constexpr int PR_TILE = PR_BLOCK * PR_ITEMS;
+constexpr int PR_WITEMS = 8;
+constexpr int PR_WTILE = 32 * PR_WITEMS;
+constexpr int PR_LONG = 8;   // split rows spanning more tiles are joined by a whole warp
 
 struct SyncWords {
-    uint32_t launch;     // last epoch used by the look-back flags
+    uint32_t launch;     // launches so far (diagnostics)
     uint32_t bar_count;  // grid barrier arrivals
     uint32_t bar_gen;    // grid barrier generation
     uint32_t done;       // last-block-done counter
-    uint32_t stop;       // latched "converged" flag of per-iteration launches
+    uint32_t stop;       // unused
     uint32_t pad[3];
+};
+
+// Fixup descriptor of a tile whose first row began in an earlier tile and
+// ends in this one: the row and the first tile holding its nonzeros.
+struct FixDesc {
+    int32_t row;   // -1: no fixup
+    int32_t ts;
 };
 
 enum GatherMode : int32_t { G_W = 0, G_TD = 1, G_ISO = 2 };
@@ -100,8 +109,11 @@ struct PrParams {
     const int32_t* tile_i = nullptr;
     const int32_t* tile_k = nullptr;
     int32_t ntiles = 0;
-    double* agg = nullptr;
-    uint32_t* flag = nullptr;
+    double* agg = nullptr;       // carry of the row open at each tile's end
+    double* first = nullptr;     // this tile's part of a split first row
+    const FixDesc* fix = nullptr;
+    const int32_t* longfix = nullptr;
+    int32_t nlong = 0;
     double* part = nullptr;      // [2][grid][2]
     SyncWords* sync = nullptr;
     int32_t* status = nullptr;
@@ -180,6 +192,9 @@ cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* 
 // Merge-path plan and the fused kernels.
 cudaError_t launch_tile_plan(cudaStream_t st, const int32_t* row_ptr, int32_t nrows, int32_t nnz, int64_t ntiles,
                              int32_t* tile_i, int32_t* tile_k);
+// Fixup table of the plan; *nlong_dev receives the number of long fixups.
+cudaError_t launch_fix_plan(cudaStream_t st, const int32_t* row_ptr, int64_t ntiles, const int32_t* tile_i,
+                            const int32_t* tile_k, FixDesc* fix, int32_t* longfix, int32_t* nlong_dev);
 // Resident CTAs per SM of the fused kernel for the given rank / gather types.
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent);
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,

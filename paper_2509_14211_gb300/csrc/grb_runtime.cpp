@@ -176,7 +176,9 @@ void matrix_unref(Matrix* A) {
         buf_free(c, p->tile_i);
         buf_free(c, p->tile_k);
         buf_free(c, p->agg);
-        buf_free(c, p->flag);
+        buf_free(c, p->first);
+        buf_free(c, p->fix);
+        buf_free(c, p->longfix);
         buf_free(c, p->part);
         buf_free(c, p->sync);
         for (auto& b : p->loop_bufs) buf_free(c, b);

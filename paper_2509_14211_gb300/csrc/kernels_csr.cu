@@ -102,7 +102,7 @@ __global__ void tile_plan_kernel(const int32_t* __restrict__ row_ptr, int32_t nr
                                  int32_t* tile_i, int32_t* tile_k) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t total = (int64_t)nrows + nnz;
-        const int64_t diag = t * PR_TILE < total ? t * PR_TILE : total;
+        const int64_t diag = t * PR_WTILE < total ? t * PR_WTILE : total;
         int64_t lo = diag - nnz > 0 ? diag - nnz : 0;
         int64_t hi = diag < nrows ? diag : nrows;
         while (lo < hi) {
@@ -112,6 +112,34 @@ __global__ void tile_plan_kernel(const int32_t* __restrict__ row_ptr, int32_t nr
         }
         tile_i[t] = (int32_t)lo;
         tile_k[t] = (int32_t)(diag - lo);
+    }
+}
+
+// A tile whose first row i0 began before the tile (tile_k > row_ptr[i0]) and
+// ends inside it (tile_i[t+1] > i0) gets a fixup: the row and the first tile
+// ts holding its nonzeros (the last tile whose start is at or before the
+// row's first nonzero).  Rows spanning more than PR_LONG tiles are listed
+// separately for a warp-wide sum.
+__global__ void fix_plan_kernel(const int32_t* __restrict__ row_ptr, int64_t ntiles, const int32_t* __restrict__ tile_i,
+                                const int32_t* __restrict__ tile_k, FixDesc* fix, int32_t* longfix, int32_t* nlong) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i0 = tile_i[t];
+        const int32_t start = row_ptr[i0];
+        FixDesc f;
+        f.row = -1;
+        f.ts = 0;
+        if (tile_k[t] > start && tile_i[t + 1] > i0) {
+            int64_t lo = 0, hi = ntiles + 1;   // first index with tile_k > start
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (tile_k[mid] <= start) lo = mid + 1;
+                else hi = mid;
+            }
+            f.row = i0;
+            f.ts = (int32_t)(lo - 1);
+            if (t - f.ts > PR_LONG) longfix[atomicAdd(nlong, 1)] = (int32_t)t;
+        }
+        fix[t] = f;
     }
 }
 
@@ -269,6 +297,14 @@ cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* 
 cudaError_t launch_tile_plan(cudaStream_t st, const int32_t* row_ptr, int32_t nrows, int32_t nnz, int64_t ntiles,
                              int32_t* tile_i, int32_t* tile_k) {
     tile_plan_kernel<<<grid_for(ntiles + 1), 256, 0, st>>>(row_ptr, nrows, nnz, ntiles, tile_i, tile_k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix_plan(cudaStream_t st, const int32_t* row_ptr, int64_t ntiles, const int32_t* tile_i,
+                            const int32_t* tile_k, FixDesc* fix, int32_t* longfix, int32_t* nlong_dev) {
+    cudaError_t e = cudaMemsetAsync(nlong_dev, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    fix_plan_kernel<<<grid_for(ntiles), 256, 0, st>>>(row_ptr, ntiles, tile_i, tile_k, fix, longfix, nlong_dev);
     return cudaGetLastError();
 }
 

@@ -9,18 +9,17 @@
 // the GPU form of the single fused loop the paper generates at `wait`
 // (§III-B, Fig. "materialize"), extended across the SpMV.
 //
-// Work decomposition: merge-path tiles.  The merge of the row-end offsets
-// row_ptr[1..n] with the nonzero indices 0..nnz-1 is cut into tiles of
-// PR_TILE items, so every CTA gets the same amount of work whatever the row
-// lengths (R-MAT in-degrees range from 0 to ~10^5).  A tile stages its row
-// ends and its gathered values in shared memory (coalesced col_idx loads),
-// each thread walks PR_ITEMS merge items, a block-wide segmented scan joins
-// rows split across threads, and rows split across tiles are joined by a
-// look-back on published per-tile carries (tiles only ever wait on lower
-// tiles, which are owned by co-resident CTAs of a cooperative launch, so the
-// waits always end; every wait is bounded anyway and reports a timeout
-// instead of hanging).  All reductions are fixed-order: results are
-// bit-reproducible run to run.
+// Work decomposition (merge path): the merge of the row-end offsets
+// row_ptr[1..n] with the nonzero indices 0..nnz-1 is cut into warp tiles of
+// PR_WTILE items, so every warp gets the same work whatever the row lengths
+// (R-MAT in-degrees range from 0 to ~10^5).  Warps are independent: a warp
+// stages its tile's row ends and gathered values in its own shared-memory
+// slice, each lane walks PR_WITEMS merge items, and a warp-wide segmented
+// scan (shuffles) joins rows split across lanes.  Rows split across tiles
+// are finished in a second phase after a grid barrier, from per-tile carries
+// (phase A writes them, phase B adds them up in a fixed order); there are no
+// cross-warp waits inside a phase, and every barrier wait is bounded.  All
+// reductions have a fixed order, so results are bit-reproducible.
 #include <climits>
 
 #include "grb_device.cuh"
@@ -29,19 +28,23 @@ namespace grb {
 
 namespace {
 
-constexpr int NW = PR_BLOCK / 32;
+constexpr int NWARP = PR_BLOCK / 32;
 constexpr uint32_t FULLMASK = 0xffffffffu;
 
 template <class T>
+struct WarpSmem {
+    int32_t rowend[PR_WTILE];
+    T val[PR_WTILE];
+    T rowsum[PR_WTILE];
+};
+
+template <class T>
 struct Smem {
-    int32_t rowend[PR_TILE];
-    T val[PR_TILE];
-    T rowsum[PR_TILE];
-    int32_t row0start;
-    int32_t wkey[NW], wpk[NW];
-    T wval[NW], wpv[NW];
-    double red[NW];
-    double red2[NW];
+    WarpSmem<T> w[NWARP];
+    double red[NWARP];
+    double red2[NWARP];
+    double bc[2];
+    int ok;
 };
 
 template <class G, bool NC>
@@ -75,16 +78,13 @@ __device__ __forceinline__ void gstore<float>(float* p, int64_t i, float x) { p[
 template <>
 __device__ __forceinline__ void gstore<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
 
-__device__ __forceinline__ void gstore_d(double* p, int64_t i, double x) { p[i] = x; }
-
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
     if (status) atomicCAS(status, 0, code);
 }
 
 // Bounded grid-wide barrier (all CTAs of a cooperative launch).  Returns
 // false when a wait ran out (status set); callers then leave the kernel.
-__device__ bool grid_sync(SyncWords* s, int32_t* status, int64_t spin_limit, uint32_t expected) {
-    __shared__ int ok_sh;
+__device__ bool grid_sync(SyncWords* s, int32_t* status, int64_t spin_limit, uint32_t expected, int* ok_sh) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -103,31 +103,31 @@ __device__ bool grid_sync(SyncWords* s, int32_t* status, int64_t spin_limit, uin
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
         if (ok && status && *(volatile int32_t*)status != 0) ok = 0;
-        ok_sh = ok;
+        *ok_sh = ok;
     }
     __syncthreads();
-    return ok_sh != 0;
+    return *ok_sh != 0;
 }
 
 // Deterministic fold of the per-CTA partials part[0..n) (pairs of doubles).
-__device__ __forceinline__ void reduce_parts(const double* part, int n, double& a, double& b, double* sh, double* sh2) {
+template <class T>
+__device__ __forceinline__ void reduce_parts(const double* part, int n, double& a, double& b, Smem<T>& sm) {
     double x = 0.0, y = 0.0;
     for (int c = threadIdx.x; c < n; c += PR_BLOCK) {
         x += ld_relaxed_f64(part + 2 * c);
         y += ld_relaxed_f64(part + 2 * c + 1);
     }
-    x = block_sum_d<PR_BLOCK>(x, sh);
-    y = block_sum_d<PR_BLOCK>(y, sh2);
-    __shared__ double bc[2];
-    if (threadIdx.x == 0) { bc[0] = x; bc[1] = y; }
+    x = block_sum_d<PR_BLOCK>(x, sm.red);
+    y = block_sum_d<PR_BLOCK>(y, sm.red2);
+    if (threadIdx.x == 0) { sm.bc[0] = x; sm.bc[1] = y; }
     __syncthreads();
-    a = bc[0];
-    b = bc[1];
+    a = sm.bc[0];
+    b = sm.bc[1];
     __syncthreads();
 }
 
@@ -148,71 +148,110 @@ struct TileIO {
     int phase32;       // mixed precision: gather from w32
 };
 
+// Everything a finished row produces: the output value, its presence, the
+// next gather value, and its residual / dangling-mass contributions.
+template <class T, class G, bool NC>
+__device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, G>& io, int64_t i, T s, bool nonempty,
+                                             double& resid, double& dang) {
+    T v;
+    bool has;
+    if (p.has_base) {
+        T b = (T)0;
+        bool bh = true;
+        if (io.tele_scalar) b = io.tele;
+        else bh = vin_get<T>(p.base, i, b);
+        if (nonempty) { v = bh ? b + s : s; has = true; }
+        else { v = b; has = bh; }
+    } else {
+        v = s;
+        has = nonempty;
+    }
+    if (!has) v = (T)0;
+    io.out[i] = v;
+    if (io.out_present) io.out_present[i] = has ? 1 : 0;
+    if (p.want_resid) resid += (double)abs_c<T>(tload<T, NC>(io.r_old, i) - v);
+    if (p.want_dang && ((__ldg(p.sinkbits + (i >> 5)) >> (i & 31)) & 1u)) dang += (double)v;
+    if (io.w_next || io.w32_next) {
+        const T q = v / __ldg(reinterpret_cast<const T*>(p.dd) + i);
+        if (io.w32_next) io.w32_next[i] = (float)q;
+        else if constexpr (sizeof(T) == 8) reinterpret_cast<double*>(io.w_next)[i] = (double)q;
+        else gstore<G>(io.w_next, i, (float)q);
+    }
+}
+
 template <class T, class G, int GMODE, bool NC>
-__device__ __forceinline__ void process_tile(const PrParams& p, int t, uint32_t epoch, const TileIO<T, G>& io,
-                                             double& resid, double& dang, Smem<T>& sm) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int32_t j) {
+    if (GMODE == G_W) {
+        if (io.phase32) return (T)gload_f<float, NC>(io.w32, j);
+        if constexpr (sizeof(T) == 8) return tload<T, NC>(reinterpret_cast<const T*>(io.w), j);
+        else return (T)gload_f<G, NC>(io.w, j);
+    } else if (GMODE == G_TD) {
+        return tload<T, NC>(io.t, j) / tload<T, NC>(io.d, j);
+    }
+    return (T)p.g_iso;
+}
+
+// Phase A for one warp tile: row sums of the rows that start and end in the
+// tile go through the epilogue; the tile's part of a first row that began
+// earlier goes to first[t]; the part of the row still open at the end goes
+// to agg[t].
+template <class T, class G, int GMODE, bool NC>
+__device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TileIO<T, G>& io, double& resid,
+                                          double& dang, WarpSmem<T>& ws) {
+    const int lane = threadIdx.x & 31;
     const int32_t i0 = __ldg(p.tile_i + t), k0 = __ldg(p.tile_k + t);
     const int32_t i1 = __ldg(p.tile_i + t + 1), k1 = __ldg(p.tile_k + t + 1);
     const int nA = i1 - i0, nB = k1 - k0;
+    const int32_t row0start = __ldg(p.row_ptr + i0);
 
-    // ---- stage row ends and gathered values
-    if (tid == 0) sm.row0start = __ldg(p.row_ptr + i0);
-    for (int x = tid; x < nA; x += PR_BLOCK) sm.rowend[x] = __ldg(p.row_ptr + i0 + 1 + x);
-    int32_t cols[PR_ITEMS];
+    // ---- stage: column indices, then the gathers; row ends
+    int32_t cols[PR_WITEMS];
 #pragma unroll
-    for (int q = 0; q < PR_ITEMS; ++q) {
-        const int y = tid + q * PR_BLOCK;
+    for (int q = 0; q < PR_WITEMS; ++q) {
+        const int y = lane + 32 * q;
         cols[q] = y < nB ? __ldg(p.col_idx + k0 + y) : 0;
     }
 #pragma unroll
-    for (int q = 0; q < PR_ITEMS; ++q) {
-        const int y = tid + q * PR_BLOCK;
-        if (y < nB) {
-            T g;
-            if (GMODE == G_W) {
-                if (io.phase32) g = (T)gload_f<float, NC>(io.w32, cols[q]);
-                else if constexpr (sizeof(T) == 8) g = tload<T, NC>(reinterpret_cast<const T*>(io.w), cols[q]);
-                else g = (T)gload_f<G, NC>(io.w, cols[q]);
-            } else if (GMODE == G_TD) {
-                g = tload<T, NC>(io.t, cols[q]) / tload<T, NC>(io.d, cols[q]);
-            } else {
-                g = (T)p.g_iso;
-            }
-            sm.val[y] = g;
-        }
+    for (int q = 0; q < PR_WITEMS; ++q) {
+        const int x = lane + 32 * q;
+        if (x < nA) ws.rowend[x] = __ldg(p.row_ptr + i0 + 1 + x);
     }
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PR_WITEMS; ++q) {
+        const int y = lane + 32 * q;
+        if (y < nB) ws.val[y] = gather<T, G, GMODE, NC>(p, io, cols[q]);
+    }
+    __syncwarp();
 
-    // ---- per-thread merge walk
+    // ---- per-lane merge walk over PR_WITEMS items
     const int total = nA + nB;
-    int d0 = tid * PR_ITEMS;
+    int d0 = lane * PR_WITEMS;
     if (d0 > total) d0 = total;
-    int d1 = d0 + PR_ITEMS;
+    int d1 = d0 + PR_WITEMS;
     if (d1 > total) d1 = total;
     int lo = d0 - nB > 0 ? d0 - nB : 0;
     int hi = d0 < nA ? d0 : nA;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (sm.rowend[mid] <= k0 + (d0 - mid - 1)) lo = mid + 1;
+        if (ws.rowend[mid] <= k0 + (d0 - mid - 1)) lo = mid + 1;
         else hi = mid;
     }
     int x = lo, y = d0 - lo;
     const int x_start = x;
     T acc = (T)0;
     for (int dd = d0; dd < d1; ++dd) {
-        if (x < nA && (y >= nB || sm.rowend[x] <= k0 + y)) {
-            sm.rowsum[x] = acc;
+        if (x < nA && (y >= nB || ws.rowend[x] <= k0 + y)) {
+            ws.rowsum[x] = acc;
             acc = (T)0;
             ++x;
         } else {
-            acc += sm.val[y];
+            acc += ws.val[y];
             ++y;
         }
     }
 
-    // ---- block-wide segmented (reduce-by-key) scan of the thread carries
-    int key = x;
+    // ---- warp segmented (reduce-by-key) scan of the lane carries
+    const int key = x;
     T val = acc;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -220,109 +259,49 @@ __device__ __forceinline__ void process_tile(const PrParams& p, int t, uint32_t 
         const T v2 = __shfl_up_sync(FULLMASK, val, off);
         if (lane >= off && k2 == key) val = v2 + val;
     }
-    if (lane == 31) { sm.wkey[warp] = key; sm.wval[warp] = val; }
-    __syncthreads();
-    if (warp == 0) {
-        int wk = lane < NW ? sm.wkey[lane] : INT_MAX;
-        T wv = lane < NW ? sm.wval[lane] : (T)0;
+    const int exk = __shfl_up_sync(FULLMASK, key, 1);
+    const T exv = __shfl_up_sync(FULLMASK, val, 1);
+    if (lane > 0 && x > x_start && exk == x_start) ws.rowsum[x_start] = exv + ws.rowsum[x_start];
+    if (lane == 31) p.agg[t] = (double)val;
+    __syncwarp();
+
+    // ---- epilogue of the rows finished here
+    const int x_lo = (k0 > row0start) ? 1 : 0;
+    if (x_lo == 1 && nA > 0 && lane == 0) p.first[t] = (double)ws.rowsum[0];
+    for (int xr = x_lo + lane; xr < nA; xr += 32) {
+        const int32_t rs = xr == 0 ? row0start : ws.rowend[xr - 1];
+        row_epilogue<T, G, NC>(p, io, (int64_t)i0 + xr, ws.rowsum[xr], ws.rowend[xr] > rs, resid, dang);
+    }
+    __syncwarp();
+}
+
+// Phase B: rows split across tiles.  Each thread takes tiles with a short
+// fixup (at most PR_LONG carries to add); each warp takes a long one.
+template <class T, class G, bool NC>
+__device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io, double& resid, double& dang) {
+    const int64_t nthreads = (int64_t)gridDim.x * PR_BLOCK;
+    for (int64_t t = (int64_t)blockIdx.x * PR_BLOCK + threadIdx.x; t < p.ntiles; t += nthreads) {
+        const FixDesc f = p.fix[t];
+        if (f.row < 0 || t - f.ts > PR_LONG) continue;
+        double sum = 0.0;
+        for (int64_t tt = f.ts; tt < t; ++tt) sum += __ldcg(p.agg + tt);
+        sum += __ldcg(p.first + t);
+        row_epilogue<T, G, NC>(p, io, f.row, (T)sum, true, resid, dang);
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * NWARP;
+    for (int64_t q = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5); q < p.nlong; q += nwarps) {
+        const int32_t t = p.longfix[q];
+        const FixDesc f = p.fix[t];
+        double sum = 0.0;
+        for (int64_t tt = f.ts + lane; tt < t; tt += 32) sum += __ldcg(p.agg + tt);
 #pragma unroll
-        for (int off = 1; off < NW; off <<= 1) {
-            const int k2 = __shfl_up_sync(FULLMASK, wk, off);
-            const T v2 = __shfl_up_sync(FULLMASK, wv, off);
-            if (lane >= off && k2 == wk) wv = v2 + wv;
-        }
-        const int ek = __shfl_up_sync(FULLMASK, wk, 1);
-        const T ev = __shfl_up_sync(FULLMASK, wv, 1);
-        if (lane < NW) {
-            sm.wpk[lane] = lane == 0 ? -1 : ek;
-            sm.wpv[lane] = lane == 0 ? (T)0 : ev;
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(FULLMASK, sum, off);
+        if (lane == 0) {
+            sum += __ldcg(p.first + t);
+            row_epilogue<T, G, NC>(p, io, f.row, (T)sum, true, resid, dang);
         }
     }
-    __syncthreads();
-    const int pk = sm.wpk[warp];
-    const T pv = sm.wpv[warp];
-    const T incl = (pk == key) ? pv + val : val;
-    int exk = __shfl_up_sync(FULLMASK, key, 1);
-    T exv = __shfl_up_sync(FULLMASK, incl, 1);
-    if (lane == 0) { exk = pk; exv = pv; }
-    if (x > x_start && exk == x_start) sm.rowsum[x_start] = exv + sm.rowsum[x_start];
-    __syncthreads();  // the look-back below updates rowsum[0] too
-
-    // ---- publish the carry of the row still open at the tile end
-    if (tid == PR_BLOCK - 1) {
-        p.agg[t] = (double)incl;
-        st_release_u32(p.flag + t, epoch);
-    }
-
-    // ---- look-back: the first row began in earlier tiles
-    if (warp == 0 && nA > 0 && k0 > sm.row0start) {
-        const int32_t rstart = sm.row0start;
-        double P = 0.0;
-        int base = t - 1;
-        bool done = false;
-        while (!done) {
-            const int tt = base - lane;
-            double v = 0.0;
-            bool stop_here = true;
-            if (tt >= 0 && __ldg(p.tile_k + tt + 1) > rstart) {
-                stop_here = __ldg(p.tile_k + tt) <= rstart;
-                int64_t spins = 0;
-                while (ld_acquire_u32(p.flag + tt) != epoch) {
-                    // give up after spin_limit polls, or at once when another
-                    // wait of this launch already gave up
-                    if (++spins > p.spin_limit || ((spins & 255) == 0 && *(volatile int32_t*)p.status != 0)) {
-                        set_status(p.status, (int32_t)GRB_DEVICE_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-                v = ld_relaxed_f64(p.agg + tt);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULLMASK, v, off);
-            P += __shfl_sync(FULLMASK, v, 0);
-            done = __any_sync(FULLMASK, stop_here);
-            base -= 32;
-        }
-        if (lane == 0) sm.rowsum[0] = (T)P + sm.rowsum[0];
-    }
-    __syncthreads();
-
-    // ---- row epilogue (coalesced over the tile's rows)
-    for (int xr = tid; xr < nA; xr += PR_BLOCK) {
-        const int64_t i = (int64_t)i0 + xr;
-        const int32_t rs = xr == 0 ? sm.row0start : sm.rowend[xr - 1];
-        const bool nonempty = sm.rowend[xr] > rs;
-        const T s = sm.rowsum[xr];
-        T v;
-        bool has;
-        if (p.has_base) {
-            T b = (T)0;
-            bool bh = true;
-            if (io.tele_scalar) b = io.tele;
-            else bh = vin_get<T>(p.base, i, b);
-            if (nonempty) { v = bh ? b + s : s; has = true; }
-            else { v = b; has = bh; }
-        } else {
-            v = s;
-            has = nonempty;
-        }
-        if (!has) v = (T)0;
-        io.out[i] = v;
-        if (io.out_present) io.out_present[i] = has ? 1 : 0;
-        if (p.want_resid) {
-            const T ro = tload<T, NC>(io.r_old, i);
-            resid += (double)abs_c<T>(ro - v);
-        }
-        if (p.want_dang && ((__ldg(p.sinkbits + (i >> 5)) >> (i & 31)) & 1u)) dang += (double)v;
-        if (io.w_next || io.w32_next) {
-            const T q = v / __ldg(reinterpret_cast<const T*>(p.dd) + i);
-            if (io.w32_next) io.w32_next[i] = (float)q;
-            else if constexpr (sizeof(T) == 8) gstore_d(reinterpret_cast<double*>(io.w_next), i, (double)q);
-            else gstore<G>(io.w_next, i, (float)q);
-        }
-    }
-    __syncthreads();
 }
 
 template <class T>
@@ -330,8 +309,9 @@ __device__ __forceinline__ T tele_value(const PrParams& p) {
     return p.tele_from_slot ? (T)round_to(p.out.type, *p.tele_slot) : (T)0;
 }
 
-// One fused body per launch (also the fast unfused mxv).  In an iterated
-// sequence (p.iters_done != null) the launch first checks the loop
+// One fused body per launch (also the fast unfused mxv): phase A, grid
+// barrier, phase B, then the last CTA folds the per-CTA partials.  In an
+// iterated sequence (p.iters_done != null) the launch first checks the loop
 // condition left by the previous launch and does nothing once it fails.
 template <class T, class G, int GMODE>
 __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant__ PrParams p) {
@@ -344,7 +324,6 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
         const int64_t done_so_far = *(volatile int64_t*)p.iters_done;
         if (!(rd > p.tol) || done_so_far != it) return;
     }
-    const uint32_t epoch = *(volatile uint32_t*)&p.sync->launch + 1u;
     TileIO<T, G> io{};
     io.tele_scalar = p.tele_from_slot;
     io.tele = tele_value<T>(p);
@@ -367,21 +346,12 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
     io.w32_next = nullptr;
     io.phase32 = 0;
     double resid = 0.0, dang = 0.0;
-    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x)
-        process_tile<T, G, GMODE, true>(p, t, epoch, io, resid, dang, sm);
-    if (!p.want_resid && !p.want_dang && !iterated) {
-        // no reductions: only the epoch counter needs the last block
-        if (threadIdx.x == 0) {
-            __threadfence();
-            last = atomicAdd(&p.sync->done, 1u) == gridDim.x - 1;
-        }
-        __syncthreads();
-        if (last && threadIdx.x == 0) {
-            p.sync->done = 0;
-            p.sync->launch = epoch;
-        }
-        return;
-    }
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * NWARP;
+    for (int t = blockIdx.x * NWARP + warp; t < p.ntiles; t += nwarps)
+        warp_tile<T, G, GMODE, true>(p, t, io, resid, dang, sm.w[warp]);
+    if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
+    fixups<T, G, true>(p, io, resid, dang);
     resid = block_sum_d<PR_BLOCK>(resid, sm.red);
     dang = block_sum_d<PR_BLOCK>(dang, sm.red2);
     if (threadIdx.x == 0) {
@@ -394,31 +364,34 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
     if (!last) return;
     __threadfence();
     double R, D;
-    reduce_parts(p.part, gridDim.x, R, D, sm.red, sm.red2);
+    reduce_parts<T>(p.part, gridDim.x, R, D, sm);
     if (threadIdx.x == 0) {
         R = round_to(p.resid_type, R);
-        if (p.resid_slot) *p.resid_slot = R;
-        if (p.dang_slot) *p.dang_slot = D;
+        if (p.resid_slot && p.want_resid) *p.resid_slot = R;
+        if (p.dang_slot && p.want_dang) *p.dang_slot = D;
         if (p.tele_slot && p.want_dang) *p.tele_slot = schain_apply(p.chain, D);
         if (iterated) {
             if (p.hist) p.hist[it] = R;
             *p.iters_done = it + 1;
         }
         p.sync->done = 0;
-        p.sync->launch = epoch;
+        p.sync->launch += 1;
     }
 }
 
 // Whole loop in one launch: prologue (w_0 = r_0 ./ d and the dangling mass of
-// r_0), then bodies separated by grid barriers while the condition holds.
+// r_0), then bodies while the condition holds; each body is phase A,
+// barrier, phase B, barrier, and every CTA folds the same partials in the
+// same order, so all CTAs take the same loop decision.
 template <class T, class G>
 __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_constant__ PrParams p) {
     __shared__ Smem<T> sm;
-    const uint32_t base_epoch = *(volatile uint32_t*)&p.sync->launch;
     const int G_ = gridDim.x;
     const T* dd = reinterpret_cast<const T*>(p.dd);
     const T* r0 = reinterpret_cast<const T*>(p.r0);
     int phase32 = 0;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = G_ * NWARP;
 
     // prologue
     double dang = 0.0;
@@ -434,14 +407,13 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
         p.part[2 * blockIdx.x] = 0.0;
         p.part[2 * blockIdx.x + 1] = dang;
     }
-    if (!grid_sync(p.sync, p.status, p.spin_limit, G_)) return;
+    if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
     double R, D;
-    reduce_parts(p.part, G_, R, D, sm.red, sm.red2);
+    reduce_parts<T>(p.part, G_, R, D, sm);
     T tele = p.tele_from_slot ? (T)round_to(p.out.type, schain_apply(p.chain, D)) : (T)0;
     double rd = p.rdiff0;
     int it = 0;
     while (it < p.iters && rd > p.tol) {
-        const uint32_t epoch = base_epoch + 1u + (uint32_t)it;
         TileIO<T, G> io{};
         io.r_old = it == 0 ? r0 : reinterpret_cast<const T*>(p.rbuf[(it - 1) & 1]);
         io.out = reinterpret_cast<T*>(p.rbuf[it & 1]);
@@ -455,8 +427,10 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
         io.tele_scalar = p.tele_from_slot;
         double resid = 0.0;
         dang = 0.0;
-        for (int t = blockIdx.x; t < p.ntiles; t += G_)
-            process_tile<T, G, G_W, false>(p, t, epoch, io, resid, dang, sm);
+        for (int t = blockIdx.x * NWARP + warp; t < p.ntiles; t += nwarps)
+            warp_tile<T, G, G_W, false>(p, t, io, resid, dang, sm.w[warp]);
+        if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
+        fixups<T, G, false>(p, io, resid, dang);
         resid = block_sum_d<PR_BLOCK>(resid, sm.red);
         dang = block_sum_d<PR_BLOCK>(dang, sm.red2);
         double* part = p.part + 2 * G_ * ((it + 1) & 1);
@@ -464,8 +438,8 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
             part[2 * blockIdx.x] = resid;
             part[2 * blockIdx.x + 1] = dang;
         }
-        if (!grid_sync(p.sync, p.status, p.spin_limit, G_)) return;
-        reduce_parts(part, G_, R, D, sm.red, sm.red2);
+        if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
+        reduce_parts<T>(part, G_, R, D, sm);
         rd = round_to(p.resid_type, R);
         if (p.tele_from_slot) tele = (T)round_to(p.out.type, schain_apply(p.chain, D));
         if (blockIdx.x == 0 && threadIdx.x == 0 && p.hist) p.hist[it] = rd;
@@ -478,7 +452,7 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
             for (int64_t i = (int64_t)blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += (int64_t)G_ * PR_BLOCK)
                 w32[i] = (float)(__ldcg(rcur + i) / dd[i]);
             phase32 = 1;
-            if (!grid_sync(p.sync, p.status, p.spin_limit, G_)) return;
+            if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -487,7 +461,7 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
         if (p.tele_slot) *p.tele_slot = (double)tele;
         *p.iters_done = it;
         if (p.mixed_phase) *p.mixed_phase = phase32;
-        p.sync->launch = base_epoch + (uint32_t)it;
+        p.sync->launch += 1;
     }
 }
 
@@ -495,7 +469,8 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
 // wait runs out after spin_limit polls and the kernel returns with
 // GRB_DEVICE_TIMEOUT in *status.  Exercises the bounded-wait path.
 __global__ void barrier_selftest_kernel(SyncWords* sync, int32_t* status, int64_t spin_limit) {
-    grid_sync(sync, status, spin_limit, gridDim.x + 1);
+    __shared__ int ok;
+    grid_sync(sync, status, spin_limit, gridDim.x + 1, &ok);
 }
 
 template <class K>
