@@ -131,7 +131,12 @@ def run_profile_case(args):
 
     torch.cuda.set_device(0)
     n = 1 << args.scale
-    src, dst = graphgen.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    src, dst = graphgen.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED, permute=not args.unpermuted)
+    if args.degree_sorted:   # relabel by descending out-degree (host side, for the experiment)
+        order = np.argsort(-np.bincount(src, minlength=n), kind="stable")
+        new_id = np.empty(n, dtype=np.int32)
+        new_id[order] = np.arange(n, dtype=np.int32)
+        src, dst = new_id[src], new_id[dst]
     ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, args.loop_mode)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
@@ -166,6 +171,8 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--iters", type=int, default=ITERS)
     ap.add_argument("--loop-mode", type=int, default=1, help="1 persistent kernel, 2 CUDA graph of fused kernels")
+    ap.add_argument("--unpermuted", action="store_true", help="profiling run on R-MAT without label scrambling")
+    ap.add_argument("--degree-sorted", action="store_true", help="profiling run with vertices relabeled by out-degree")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

@@ -55,7 +55,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+            # GRB_NVCC_FLAGS: extra -D tuning knobs (e.g. -DPR_MINBLOCKS=4)
+            extra = os.environ.get("GRB_NVCC_FLAGS", "").split()
+            cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *extra,
                    "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj + ".tmp"]
             jobs.append((cmd, obj))
 

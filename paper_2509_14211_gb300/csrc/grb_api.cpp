@@ -337,7 +337,7 @@ grb_info grb_matrix_build_csr(grb_matrix* Aout, grb_context ctx, grb_type type, 
             A->row_ptr.p = rp;
             A->row_ptr.bytes = sizeof(int32_t) * (nrows + 1);
             A->col_idx.p = ci;
-            A->col_idx.bytes = sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1);
+            A->col_idx.bytes = sizeof(int32_t) * (size_t)padded_nnz(nnz);
             A->vals.p = vv;
             A->vals.bytes = vv ? esz * (size_t)(nnz > 0 ? nnz : 1) : 0;
             DevBuf cnt = buf_alloc(c, sizeof(unsigned long long));

@@ -92,7 +92,10 @@ struct Node {
 // Cached launch plan of a CSR matrix for the merge-path kernels.
 struct TilePlan {
     int64_t ntiles = 0;
-    DevBuf tile_i, tile_k;     // merge-path coordinates of each tile start (ntiles+1)
+    DevBuf meta;               // per tile: first non-empty row | continues-a-row << 31
+    DevBuf rowend_bits;        // bit k: nonzero k ends its row
+    DevBuf ne_rows, empty_rows;
+    int64_t n_ne = 0, n_empty = 0;
     DevBuf agg, first;         // per-tile carry of the open last row / partial of the first row
     DevBuf fix;                // per-tile fixup descriptor (row of a split first row, first tile of it)
     DevBuf longfix;            // tiles whose split first row spans more than PR_LONG tiles

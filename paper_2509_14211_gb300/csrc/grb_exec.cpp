@@ -135,36 +135,47 @@ static void sem_ops(grb_semiring s, int32_t& add, int32_t& mul) {
 grb_info ensure_plan(Ctx* c, Matrix* A) {
     if (A->plan) return GRB_SUCCESS;
     TilePlan* p = new TilePlan();
-    const int64_t total = A->nrows + A->nnz;
-    p->ntiles = (total + PR_WTILE - 1) / PR_WTILE;
-    if (p->ntiles < 1) p->ntiles = 1;
-    p->tile_i = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 1));
-    p->tile_k = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 1));
+    p->ntiles = padded_nnz(A->nnz) / PR_NZTILE;
+    const int64_t n = A->nrows;
+    p->meta = buf_alloc(c, sizeof(uint32_t) * p->ntiles);
+    p->rowend_bits = buf_alloc(c, sizeof(uint32_t) * (size_t)p->ntiles * (PR_NZTILE / 32));
+    p->ne_rows = buf_alloc(c, sizeof(int32_t) * n);
+    p->empty_rows = buf_alloc(c, sizeof(int32_t) * n);
     p->agg = buf_alloc(c, sizeof(double) * p->ntiles);
     p->first = buf_alloc(c, sizeof(double) * p->ntiles);
     p->fix = buf_alloc(c, sizeof(FixDesc) * p->ntiles);
-    p->longfix = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 1));
+    p->longfix = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 3));
     p->part = buf_alloc(c, sizeof(double) * 2 * 2 * (size_t)c->sm_count * 8);
     p->sync = buf_alloc(c, sizeof(SyncWords));
     A->plan = p;
-    if (!p->tile_i.p || !p->tile_k.p || !p->agg.p || !p->first.p || !p->fix.p || !p->longfix.p || !p->part.p ||
-        !p->sync.p)
+    if (!p->meta.p || !p->rowend_bits.p || !p->ne_rows.p || !p->empty_rows.p || !p->agg.p || !p->first.p ||
+        !p->fix.p || !p->longfix.p || !p->part.p || !p->sync.p)
         return GRB_OUT_OF_MEMORY;
-    int32_t* nlong_dev = (int32_t*)p->longfix.p + p->ntiles;
-    grb_info st = cuda_check(c, launch_tile_plan(c->stream, (const int32_t*)A->row_ptr.p, (int32_t)A->nrows,
-                                                 (int32_t)A->nnz, p->ntiles, (int32_t*)p->tile_i.p,
-                                                 (int32_t*)p->tile_k.p), "tile plan");
-    if (!st)
-        st = cuda_check(c, launch_fix_plan(c->stream, (const int32_t*)A->row_ptr.p, p->ntiles,
-                                           (const int32_t*)p->tile_i.p, (const int32_t*)p->tile_k.p,
-                                           (FixDesc*)p->fix.p, (int32_t*)p->longfix.p, nlong_dev), "fixup plan");
+    int32_t* counts_dev = (int32_t*)p->longfix.p + p->ntiles;
+    PlanArgs pa;
+    pa.row_ptr = (const int32_t*)A->row_ptr.p;
+    pa.nrows = (int32_t)A->nrows;
+    pa.nnz = (int32_t)A->nnz;
+    pa.ntiles = p->ntiles;
+    pa.ne_rows = (int32_t*)p->ne_rows.p;
+    pa.empty_rows = (int32_t*)p->empty_rows.p;
+    pa.rowend_bits = (uint32_t*)p->rowend_bits.p;
+    pa.tile_meta = (uint32_t*)p->meta.p;
+    pa.fix = (FixDesc*)p->fix.p;
+    pa.longfix = (int32_t*)p->longfix.p;
+    pa.counts = counts_dev;
+    grb_info st = cuda_check(c, build_row_plan(c->stream, pa, [](void* x, size_t b) { return dev_alloc((Ctx*)x, b); },
+                                               [](void* x, void* q, size_t b) { dev_free((Ctx*)x, q, b); }, c),
+                             "row plan");
     if (st) return st;
-    c->stats.kernel_launches += 2;
-    int32_t nlong = 0;
-    st = cuda_check(c, cudaMemcpyAsync(&nlong, nlong_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "plan");
+    c->stats.kernel_launches += 5;
+    int32_t counts[3] = {0, 0, 0};
+    st = cuda_check(c, cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, c->stream), "plan");
     if (!st) st = cuda_check(c, cudaMemsetAsync(p->sync.p, 0, sizeof(SyncWords), c->stream), "plan sync");
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "plan");
-    p->nlong = nlong;
+    p->n_ne = counts[0];
+    p->n_empty = counts[1];
+    p->nlong = counts[2];
     return st;
 }
 
@@ -183,9 +194,13 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
     p.col_idx = (const int32_t*)A->col_idx.p;
     p.nrows = (int32_t)A->nrows;
     p.nnz = (int32_t)A->nnz;
-    p.tile_i = (const int32_t*)pl->tile_i.p;
-    p.tile_k = (const int32_t*)pl->tile_k.p;
     p.ntiles = (int32_t)pl->ntiles;
+    p.tile_meta = (const uint32_t*)pl->meta.p;
+    p.rowend_bits = (const uint32_t*)pl->rowend_bits.p;
+    p.ne_rows = (const int32_t*)pl->ne_rows.p;
+    p.n_ne = (int32_t)pl->n_ne;
+    p.empty_rows = (const int32_t*)pl->empty_rows.p;
+    p.n_empty = (int32_t)pl->n_empty;
     p.agg = (double*)pl->agg.p;
     p.first = (double*)pl->first.p;
     p.fix = (const FixDesc*)pl->fix.p;

@@ -110,7 +110,8 @@ bool match_body(Version* r0, Version* Vr, Version* Vc, LoopMatch& lm) {
                 lm.rt = o;
             }
         }
-        if (!M || !invariant_full(lm.rt, T, true)) return false;
+        // the loop kernels take the teleport as one scalar: rt must be iso
+        if (!M || !invariant_full(lm.rt, T, true) || lm.rt->fmt != Fmt::ISO) return false;
     } else if (R->k == OpK::MXV && R->has_accum && R->accum.opcode == GRB_PLUS) {
         M = R;
         Version* av = R->w_old;
@@ -284,7 +285,8 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
         p.sinkbits = (const uint32_t*)lm.sinks->sinkbits.p;
         p.chain = lm.chain;
     } else {
-        p.base = vin_of(lm.rt);
+        p.tele_from_slot = 0;
+        p.tele_const = lm.rt->iso;   // iso teleport vector (required by the match)
     }
     p.want_resid = 1;
     p.resid_slot = sl + 1;
@@ -317,7 +319,7 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     } else if (!st) {
         // prologue (no bodies) + one fused kernel per body, as a CUDA graph
         const int pgrid = pr_grid(c, A, T, G, G_W, 1);
-        const int igrid = pr_grid(c, A, T, G, G_W, 0);
+        const int igrid = pr_grid(c, A, T, G, G_W, 2);
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         // capture on a private stream (the context's stream may be the
@@ -335,7 +337,7 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
             for (int it = 0; it < iters && e == cudaSuccess; ++it) {
                 PrParams pi = p;
                 pi.iter_index = it;
-                e = launch_pr(c->capture_stream, pi, T, G, igrid, 0);
+                e = launch_pr(c->capture_stream, pi, T, G, igrid, 2);
             }
             cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &graph);
             st = cuda_check(c, e != cudaSuccess ? e : e2, "graph capture");

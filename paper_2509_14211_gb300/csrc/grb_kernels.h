@@ -70,12 +70,18 @@ struct WriteSpec {
     VIn w_old;
 };
 
-// Merge-path tile plan of a CSR matrix: every warp takes tiles of
-// PR_WTILE merge items (row ends + nonzeros), PR_WITEMS per lane.
+// Row-gather plan of a CSR matrix: every warp takes tiles of PR_NZTILE
+// consecutive nonzeros, PR_NZLANE per lane.
 constexpr int PR_BLOCK = 256;
-constexpr int PR_WITEMS = 8;
-constexpr int PR_WTILE = 32 * PR_WITEMS;
+constexpr int PR_NZLANE = 8;
+constexpr int PR_NZTILE = 32 * PR_NZLANE;
 constexpr int PR_LONG = 8;   // split rows spanning more tiles are joined by a whole warp
+
+// col_idx arrays are allocated to a whole number of tiles (padding = col 0).
+inline int64_t padded_nnz(int64_t nnz) {
+    const int64_t t = (nnz > 0 ? nnz : 1) + PR_NZTILE - 1;
+    return t / PR_NZTILE * PR_NZTILE;
+}
 
 struct SyncWords {
     uint32_t launch;     // launches so far (diagnostics)
@@ -104,11 +110,15 @@ enum GatherMode : int32_t { G_W = 0, G_TD = 1, G_ISO = 2 };
 struct PrParams {
     // matrix and plan
     const int32_t* row_ptr = nullptr;
-    const int32_t* col_idx = nullptr;
+    const int32_t* col_idx = nullptr;   // padded to ntiles * PR_NZTILE
     int32_t nrows = 0, nnz = 0;
-    const int32_t* tile_i = nullptr;
-    const int32_t* tile_k = nullptr;
     int32_t ntiles = 0;
+    const uint32_t* tile_meta = nullptr;  // first non-empty row of the tile | (continues a row) << 31
+    const uint32_t* rowend_bits = nullptr;  // bit k: nonzero k is the last of its row
+    const int32_t* ne_rows = nullptr;     // the non-empty rows, ascending
+    int32_t n_ne = 0;
+    const int32_t* empty_rows = nullptr;  // the empty rows, ascending
+    int32_t n_empty = 0;
     double* agg = nullptr;       // carry of the row open at each tile's end
     double* first = nullptr;     // this tile's part of a split first row
     const FixDesc* fix = nullptr;
@@ -150,6 +160,7 @@ struct PrParams {
     void* wbuf[2] = {nullptr, nullptr};
     double rdiff0 = 1.0;         // value of the loop condition before body 0
     int32_t tele_from_slot = 0;  // base is the scalar tele_slot (uniform dangling)
+    double tele_const = 0.0;     // PageRank loops without it: the iso teleport value
     // mixed precision (BF16 gather until the residual drops below mixed_switch)
     int32_t mixed = 0;
     double mixed_switch = 1e-3;
@@ -190,11 +201,23 @@ cudaError_t launch_col_degree(cudaStream_t st, int64_t ncols, int64_t nnz, const
 cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* row_ptr, unsigned long long* out);
 
 // Merge-path plan and the fused kernels.
-cudaError_t launch_tile_plan(cudaStream_t st, const int32_t* row_ptr, int32_t nrows, int32_t nnz, int64_t ntiles,
-                             int32_t* tile_i, int32_t* tile_k);
-// Fixup table of the plan; *nlong_dev receives the number of long fixups.
-cudaError_t launch_fix_plan(cudaStream_t st, const int32_t* row_ptr, int64_t ntiles, const int32_t* tile_i,
-                            const int32_t* tile_k, FixDesc* fix, int32_t* longfix, int32_t* nlong_dev);
+// Row-gather plan: the non-empty / empty row lists, the row-end bitmap, the
+// per-tile metadata and fixup table.  Device outputs are preallocated by
+// the caller (ne_rows/empty_rows: nrows each, bits: ntiles*PR_NZTILE/32,
+// meta/fix: ntiles, longfix: ntiles); counts[0..2] = n_ne, n_empty, nlong.
+struct PlanArgs {
+    const int32_t* row_ptr;
+    int32_t nrows, nnz;
+    int64_t ntiles;
+    int32_t* ne_rows;
+    int32_t* empty_rows;
+    uint32_t* rowend_bits;
+    uint32_t* tile_meta;
+    FixDesc* fix;
+    int32_t* longfix;
+    int32_t* counts;
+};
+cudaError_t build_row_plan(cudaStream_t st, const PlanArgs& a, AllocFn af, FreeFn ff, void* actx);
 // Resident CTAs per SM of the fused kernel for the given rank / gather types.
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent);
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,

@@ -173,8 +173,10 @@ void matrix_unref(Matrix* A) {
     buf_free(c, A->vals);
     if (A->plan) {
         TilePlan* p = A->plan;
-        buf_free(c, p->tile_i);
-        buf_free(c, p->tile_k);
+        buf_free(c, p->meta);
+        buf_free(c, p->rowend_bits);
+        buf_free(c, p->ne_rows);
+        buf_free(c, p->empty_rows);
         buf_free(c, p->agg);
         buf_free(c, p->first);
         buf_free(c, p->fix);

@@ -8,6 +8,7 @@
 // the out-of-range row `nrows` so that they sort last and are cut off), then
 // split the keys into col_idx and derive row_ptr from the row boundaries.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 #include <cub/device/device_select.cuh>
 
 #include <climits>
@@ -95,50 +96,77 @@ __global__ void nonempty_kernel(int64_t nrows, const int32_t* row_ptr, unsigned 
     if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
 }
 
-// Merge-path coordinates (rows consumed, nonzeros consumed) of the start of
-// every tile: the merge of the row-end offsets row_ptr[1..n] with the
-// nonzero indices 0..nnz-1, a row end taken first on ties.
-__global__ void tile_plan_kernel(const int32_t* __restrict__ row_ptr, int32_t nrows, int32_t nnz, int64_t ntiles,
-                                 int32_t* tile_i, int32_t* tile_k) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t total = (int64_t)nrows + nnz;
-        const int64_t diag = t * PR_WTILE < total ? t * PR_WTILE : total;
-        int64_t lo = diag - nnz > 0 ? diag - nnz : 0;
-        int64_t hi = diag < nrows ? diag : nrows;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)row_ptr[mid + 1] <= diag - mid - 1) lo = mid + 1;
-            else hi = mid;
-        }
-        tile_i[t] = (int32_t)lo;
-        tile_k[t] = (int32_t)(diag - lo);
+// ---------------------------------------------------------- row plan
+// Ordered split of the rows into non-empty and empty ones: block b covers
+// rows [256b, 256b+256); pass 1 counts its non-empty rows, an exclusive scan
+// gives offsets, pass 2 writes both lists in ascending order.
+__global__ void row_count_kernel(int32_t nrows, const int32_t* __restrict__ row_ptr, int32_t* block_counts) {
+    const int32_t i = blockIdx.x * 256 + threadIdx.x;
+    const bool ne = i < nrows && row_ptr[i + 1] > row_ptr[i];
+    const int c = __syncthreads_count(ne);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = c;
+}
+
+__global__ void row_split_kernel(int32_t nrows, const int32_t* __restrict__ row_ptr, const int32_t* block_off,
+                                 int32_t* ne_rows, int32_t* empty_rows) {
+    __shared__ int warp_ne[8];
+    const int32_t i = blockIdx.x * 256 + threadIdx.x;
+    const bool valid = i < nrows;
+    const bool ne = valid && row_ptr[i + 1] > row_ptr[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ball = __ballot_sync(0xffffffffu, ne);
+    if (lane == 0) warp_ne[warp] = __popc(ball);
+    __syncthreads();
+    int before_ne = 0;
+    for (int w = 0; w < warp; ++w) before_ne += warp_ne[w];
+    before_ne += __popc(ball & ((1u << lane) - 1u));
+    const int32_t ne_off = block_off[blockIdx.x] + before_ne;
+    if (ne) ne_rows[ne_off] = i;
+    else if (valid) empty_rows[(blockIdx.x * 256 - block_off[blockIdx.x]) + (threadIdx.x - before_ne)] = i;
+}
+
+// Bit (end-1) of every non-empty row: its last nonzero.
+__global__ void rowend_bits_kernel(int32_t n_ne, const int32_t* __restrict__ ne_rows,
+                                   const int32_t* __restrict__ row_ptr, uint32_t* bits) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_ne; r += gridDim.x * blockDim.x) {
+        const int32_t k = row_ptr[ne_rows[r] + 1] - 1;
+        atomicOr(&bits[k >> 5], 1u << (k & 31));
     }
 }
 
-// A tile whose first row i0 began before the tile (tile_k > row_ptr[i0]) and
-// ends inside it (tile_i[t+1] > i0) gets a fixup: the row and the first tile
-// ts holding its nonzeros (the last tile whose start is at or before the
-// row's first nonzero).  Rows spanning more than PR_LONG tiles are listed
-// separately for a warp-wide sum.
-__global__ void fix_plan_kernel(const int32_t* __restrict__ row_ptr, int64_t ntiles, const int32_t* __restrict__ tile_i,
-                                const int32_t* __restrict__ tile_k, FixDesc* fix, int32_t* longfix, int32_t* nlong) {
+// Tile t covers nonzeros [t*PR_NZTILE, (t+1)*PR_NZTILE).  Its first row is the
+// non-empty row holding nonzero t*PR_NZTILE; bit 31 marks that this row began
+// in an earlier tile.  Such a row that also ends in tile t gets a fixup: the
+// row and the tile ts holding its first nonzero.  Rows spanning more than
+// PR_LONG tiles are listed separately for a warp-wide sum.
+__global__ void tile_meta_kernel(int64_t ntiles, int32_t n_ne, const int32_t* __restrict__ ne_rows,
+                                 const int32_t* __restrict__ row_ptr, uint32_t* meta, FixDesc* fix, int32_t* longfix,
+                                 int32_t* nlong) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i0 = tile_i[t];
-        const int32_t start = row_ptr[i0];
+        const int64_t k0 = t * PR_NZTILE;
+        int32_t lo = 0, hi = n_ne;    // first non-empty row whose end is past k0
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if ((int64_t)row_ptr[ne_rows[mid] + 1] <= k0) lo = mid + 1;
+            else hi = mid;
+        }
         FixDesc f;
         f.row = -1;
         f.ts = 0;
-        if (tile_k[t] > start && tile_i[t + 1] > i0) {
-            int64_t lo = 0, hi = ntiles + 1;   // first index with tile_k > start
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (tile_k[mid] <= start) lo = mid + 1;
-                else hi = mid;
+        uint32_t cont = 0;
+        if (lo < n_ne) {
+            const int32_t i = ne_rows[lo];
+            const int64_t start = row_ptr[i], end = row_ptr[i + 1];
+            if (start < k0) {
+                cont = 1;
+                if (end <= k0 + PR_NZTILE) {
+                    f.row = i;
+                    f.ts = (int32_t)(start / PR_NZTILE);
+                    if (t - f.ts > PR_LONG) longfix[atomicAdd(nlong, 1)] = (int32_t)t;
+                }
             }
-            f.row = i0;
-            f.ts = (int32_t)(lo - 1);
-            if (t - f.ts > PR_LONG) longfix[atomicAdd(nlong, 1)] = (int32_t)t;
         }
+        meta[t] = (uint32_t)lo | (cont << 31);
         fix[t] = f;
     }
 }
@@ -251,15 +279,19 @@ cudaError_t csr_build(cudaStream_t st, const CsrBuildArgs& a, AllocFn af, FreeFn
     if ((err = cudaMemcpyAsync(&nv, counts + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return err;
     if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
 
+    // col_idx is padded with column 0 to a whole number of nonzero tiles so
+    // that the row-gather kernels can load it in aligned 16-byte pieces
+    const int64_t npad = padded_nnz(nv);
     int32_t* row_ptr = (int32_t*)af(actx, sizeof(int32_t) * (a.nrows + 1));
-    int32_t* col_idx = (int32_t*)af(actx, sizeof(int32_t) * (nv > 0 ? nv : 1));
+    int32_t* col_idx = (int32_t*)af(actx, sizeof(int32_t) * npad);
     void* vals = a.vals ? af(actx, (size_t)esize * (nv > 0 ? nv : 1)) : nullptr;
     if (!row_ptr || !col_idx || (a.vals && !vals)) {
         if (row_ptr) ff(actx, row_ptr, sizeof(int32_t) * (a.nrows + 1));
-        if (col_idx) ff(actx, col_idx, sizeof(int32_t) * (nv > 0 ? nv : 1));
+        if (col_idx) ff(actx, col_idx, sizeof(int32_t) * npad);
         if (vals) ff(actx, vals, (size_t)esize * (nv > 0 ? nv : 1));
         return cudaErrorMemoryAllocation;
     }
+    if ((err = cudaMemsetAsync(col_idx + nv, 0, sizeof(int32_t) * (npad - nv), st)) != cudaSuccess) return err;
     if (nv == 0) {
         if ((err = cudaMemsetAsync(row_ptr, 0, sizeof(int32_t) * (a.nrows + 1), st)) != cudaSuccess) return err;
     } else {
@@ -294,18 +326,41 @@ cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_plan(cudaStream_t st, const int32_t* row_ptr, int32_t nrows, int32_t nnz, int64_t ntiles,
-                             int32_t* tile_i, int32_t* tile_k) {
-    tile_plan_kernel<<<grid_for(ntiles + 1), 256, 0, st>>>(row_ptr, nrows, nnz, ntiles, tile_i, tile_k);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fix_plan(cudaStream_t st, const int32_t* row_ptr, int64_t ntiles, const int32_t* tile_i,
-                            const int32_t* tile_k, FixDesc* fix, int32_t* longfix, int32_t* nlong_dev) {
-    cudaError_t e = cudaMemsetAsync(nlong_dev, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
-    fix_plan_kernel<<<grid_for(ntiles), 256, 0, st>>>(row_ptr, ntiles, tile_i, tile_k, fix, longfix, nlong_dev);
-    return cudaGetLastError();
+cudaError_t build_row_plan(cudaStream_t st, const PlanArgs& a, AllocFn af, FreeFn ff, void* actx) {
+    Scratch S{af, ff, actx, {}};
+    cudaError_t e;
+    const int32_t nblk = (a.nrows + 255) / 256;
+    int32_t* bc = (int32_t*)S.get(sizeof(int32_t) * (nblk + 1));
+    int32_t* bo = (int32_t*)S.get(sizeof(int32_t) * (nblk + 1));
+    if (!bc || !bo) return cudaErrorMemoryAllocation;
+    row_count_kernel<<<nblk, 256, 0, st>>>(a.nrows, a.row_ptr, bc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    size_t tb = 0;
+    if ((e = cub::DeviceScan::ExclusiveSum(nullptr, tb, bc, bo, nblk + 1, st)) != cudaSuccess) return e;
+    void* tmp = S.get(tb);
+    if (!tmp) return cudaErrorMemoryAllocation;
+    // bc[nblk] must be 0 so that bo[nblk] is the total
+    if ((e = cudaMemsetAsync(bc + nblk, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cub::DeviceScan::ExclusiveSum(tmp, tb, bc, bo, nblk + 1, st)) != cudaSuccess) return e;
+    row_split_kernel<<<nblk, 256, 0, st>>>(a.nrows, a.row_ptr, bo, a.ne_rows, a.empty_rows);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int32_t n_ne = 0;
+    if ((e = cudaMemcpyAsync(&n_ne, bo + nblk, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    const size_t nbits_words = (size_t)a.ntiles * PR_NZTILE / 32;
+    if ((e = cudaMemsetAsync(a.rowend_bits, 0, sizeof(uint32_t) * nbits_words, st)) != cudaSuccess) return e;
+    if (n_ne > 0) {
+        rowend_bits_kernel<<<grid_for(n_ne), 256, 0, st>>>(n_ne, a.ne_rows, a.row_ptr, a.rowend_bits);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemsetAsync(a.counts + 2, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+    tile_meta_kernel<<<grid_for(a.ntiles), 256, 0, st>>>(a.ntiles, n_ne, a.ne_rows, a.row_ptr, a.tile_meta, a.fix,
+                                                          a.longfix, a.counts + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int32_t counts01[2] = {n_ne, a.nrows - n_ne};
+    if ((e = cudaMemcpyAsync(a.counts, counts01, sizeof(counts01), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(st);
 }
 
 }  // namespace grb

@@ -9,17 +9,26 @@
 // the GPU form of the single fused loop the paper generates at `wait`
 // (§III-B, Fig. "materialize"), extended across the SpMV.
 //
-// Work decomposition (merge path): the merge of the row-end offsets
-// row_ptr[1..n] with the nonzero indices 0..nnz-1 is cut into warp tiles of
-// PR_WTILE items, so every warp gets the same work whatever the row lengths
-// (R-MAT in-degrees range from 0 to ~10^5).  Warps are independent: a warp
-// stages its tile's row ends and gathered values in its own shared-memory
-// slice, each lane walks PR_WITEMS merge items, and a warp-wide segmented
-// scan (shuffles) joins rows split across lanes.  Rows split across tiles
-// are finished in a second phase after a grid barrier, from per-tile carries
-// (phase A writes them, phase B adds them up in a fixed order); there are no
-// cross-warp waits inside a phase, and every barrier wait is bounded.  All
-// reductions have a fixed order, so results are bit-reproducible.
+// Work decomposition: the nonzeros are cut into warp tiles of PR_NZTILE
+// consecutive entries (PR_NZLANE per lane, loaded as two 16-byte pieces), so
+// every warp gets the same gather work whatever the row lengths (R-MAT
+// in-degrees range from 0 to ~10^5).  A bitmap marks the last nonzero of
+// every row, so a lane finds its row boundaries with a popc and a shift;
+// rows are numbered in the compressed list of non-empty rows, and the empty
+// rows (~40% of an R-MAT graph) get their epilogue in a separate streaming
+// loop.  Warps are independent: per-lane segmented sums go to the warp's
+// shared-memory slice, and a warp-wide segmented scan (shuffles) joins rows
+// split across lanes.  Rows split across tiles are finished in a second
+// phase after a grid barrier, from per-tile carries (phase A writes them,
+// phase B adds them up in a fixed order); there are no cross-warp waits
+// inside a phase, and every barrier wait is bounded.  All reductions have a
+// fixed order, so results are bit-reproducible.
+//
+// Two epilogue flavours: LEAN (the PageRank loop: scalar teleport base,
+// residual and next gather value always produced, no presence array) is
+// compiled separately from the general one the planner uses for other
+// fused groups and for the unfused mxv, so the loop's per-row code carries
+// no run-time configuration checks.
 #include <climits>
 
 #include "grb_device.cuh"
@@ -31,11 +40,31 @@ namespace {
 constexpr int NWARP = PR_BLOCK / 32;
 constexpr uint32_t FULLMASK = 0xffffffffu;
 
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef PR_MINBLOCKS
+#define PR_MINBLOCKS 4
+#endif
+// 1: load the use-once matrix arrays with evict-first (streaming) hints.
+#ifndef PR_STREAM_HINTS
+#define PR_STREAM_HINTS 1
+#endif
+// 1: ask for the largest L1 / smallest shared-memory carveout.
+#ifndef PR_MAX_L1
+#define PR_MAX_L1 0
+#endif
+
+template <class X>
+__device__ __forceinline__ X ld_stream(const X* p) {
+#if PR_STREAM_HINTS
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
+}
+
 template <class T>
 struct WarpSmem {
-    int32_t rowend[PR_WTILE];
-    T val[PR_WTILE];
-    T rowsum[PR_WTILE];
+    T rowsum[PR_NZTILE];   // sums of the rows ending in the warp's current tile
 };
 
 template <class T>
@@ -47,36 +76,42 @@ struct Smem {
     int ok;
 };
 
+// Loads of vectors that a kernel also writes.  NC: the data was written by
+// an earlier launch, so the read-only path is safe.  Otherwise (persistent
+// kernel) the data was written by other CTAs before a grid barrier; a plain
+// L1-cached load is still correct because the barrier's gpu-scope acquire
+// (ld.acquire + fence) orders it after those writes, and the hardware
+// invalidates the SM's L1 on such an acquire.
 template <class G, bool NC>
-__device__ __forceinline__ float gload_f(const G* p, int64_t j);
+__device__ __forceinline__ float gload_f(const G* p, int j);
 
 template <>
-__device__ __forceinline__ float gload_f<float, true>(const float* p, int64_t j) { return __ldg(p + j); }
+__device__ __forceinline__ float gload_f<float, true>(const float* p, int j) { return __ldg(p + j); }
 template <>
-__device__ __forceinline__ float gload_f<float, false>(const float* p, int64_t j) { return __ldcg(p + j); }
+__device__ __forceinline__ float gload_f<float, false>(const float* p, int j) { return __ldca(p + j); }
 template <>
-__device__ __forceinline__ float gload_f<__nv_bfloat16, true>(const __nv_bfloat16* p, int64_t j) {
+__device__ __forceinline__ float gload_f<__nv_bfloat16, true>(const __nv_bfloat16* p, int j) {
     const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p) + j);
     return __uint_as_float(((uint32_t)b) << 16);
 }
 template <>
-__device__ __forceinline__ float gload_f<__nv_bfloat16, false>(const __nv_bfloat16* p, int64_t j) {
-    const unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p) + j);
+__device__ __forceinline__ float gload_f<__nv_bfloat16, false>(const __nv_bfloat16* p, int j) {
+    const unsigned short b = __ldca(reinterpret_cast<const unsigned short*>(p) + j);
     return __uint_as_float(((uint32_t)b) << 16);
 }
 
 template <class T, bool NC>
-__device__ __forceinline__ T tload(const T* p, int64_t j) {
+__device__ __forceinline__ T tload(const T* p, int j) {
     if (NC) return __ldg(p + j);
-    return __ldcg(p + j);
+    return __ldca(p + j);
 }
 
 template <class G>
-__device__ __forceinline__ void gstore(G* p, int64_t i, float x);
+__device__ __forceinline__ void gstore(G* p, int i, float x);
 template <>
-__device__ __forceinline__ void gstore<float>(float* p, int64_t i, float x) { p[i] = x; }
+__device__ __forceinline__ void gstore<float>(float* p, int i, float x) { p[i] = x; }
 template <>
-__device__ __forceinline__ void gstore<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, float x) { p[i] = __float2bfloat16_rn(x); }
+__device__ __forceinline__ void gstore<__nv_bfloat16>(__nv_bfloat16* p, int i, float x) { p[i] = __float2bfloat16_rn(x); }
 
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
     if (status) atomicCAS(status, 0, code);
@@ -131,6 +166,30 @@ __device__ __forceinline__ void reduce_parts(const double* part, int n, double& 
     __syncthreads();
 }
 
+// Per-lane running sums of the residual and the dangling mass.  GB300's
+// FP64 pipe is narrow, so for FP32 ranks each lane keeps a compensated
+// (Kahan) FP32 sum -- error independent of the number of terms -- and hands
+// it to the FP64 cross-thread reduction once per body.  FP64 ranks sum in
+// FP64.
+template <class T>
+struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T x) { s += (double)x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Per-launch view of the gather / epilogue buffers.
 template <class T, class G>
 struct TileIO {
@@ -148,12 +207,43 @@ struct TileIO {
     int phase32;       // mixed precision: gather from w32
 };
 
+// Epilogue inputs of one row, loaded ahead of use.
+template <class T>
+struct RowIn {
+    T rold;
+    T dd;
+    uint32_t sinkword;
+};
+
+template <class T, class G, bool NC, bool LEAN>
+__device__ __forceinline__ RowIn<T> row_inputs(const PrParams& p, const TileIO<T, G>& io, int i) {
+    RowIn<T> in;
+    in.rold = (T)0;
+    in.dd = (T)1;
+    in.sinkword = 0;
+    if (LEAN || p.want_resid) in.rold = tload<T, NC>(io.r_old, i);
+    if (LEAN || io.w_next || io.w32_next) in.dd = __ldg(reinterpret_cast<const T*>(p.dd) + i);
+    if (p.want_dang) in.sinkword = __ldg(p.sinkbits + (i >> 5));
+    return in;
+}
+
 // Everything a finished row produces: the output value, its presence, the
 // next gather value, and its residual / dangling-mass contributions.
-template <class T, class G, bool NC>
-__device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, G>& io, int64_t i, T s, bool nonempty,
-                                             double& resid, double& dang) {
+template <class T, class G, bool LEAN>
+__device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, G>& io, int i, T s, bool nonempty,
+                                             const RowIn<T>& in, Acc<T>& resid, Acc<T>& dang) {
     T v;
+    if (LEAN) {
+        v = nonempty ? io.tele + s : io.tele;
+        io.out[i] = v;
+        resid.add(abs_c<T>(in.rold - v));
+        if (p.want_dang && ((in.sinkword >> (i & 31)) & 1u)) dang.add(v);
+        const T q = v / in.dd;
+        if (io.phase32) io.w32_next[i] = (float)q;
+        else if constexpr (sizeof(T) == 8) reinterpret_cast<double*>(io.w_next)[i] = (double)q;
+        else gstore<G>(io.w_next, i, (float)q);
+        return;
+    }
     bool has;
     if (p.has_base) {
         T b = (T)0;
@@ -169,10 +259,10 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
     if (!has) v = (T)0;
     io.out[i] = v;
     if (io.out_present) io.out_present[i] = has ? 1 : 0;
-    if (p.want_resid) resid += (double)abs_c<T>(tload<T, NC>(io.r_old, i) - v);
-    if (p.want_dang && ((__ldg(p.sinkbits + (i >> 5)) >> (i & 31)) & 1u)) dang += (double)v;
+    if (p.want_resid) resid.add(abs_c<T>(in.rold - v));
+    if (p.want_dang && ((in.sinkword >> (i & 31)) & 1u)) dang.add(v);
     if (io.w_next || io.w32_next) {
-        const T q = v / __ldg(reinterpret_cast<const T*>(p.dd) + i);
+        const T q = v / in.dd;
         if (io.w32_next) io.w32_next[i] = (float)q;
         else if constexpr (sizeof(T) == 8) reinterpret_cast<double*>(io.w_next)[i] = (double)q;
         else gstore<G>(io.w_next, i, (float)q);
@@ -180,7 +270,7 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
 }
 
 template <class T, class G, int GMODE, bool NC>
-__device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int32_t j) {
+__device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int j) {
     if (GMODE == G_W) {
         if (io.phase32) return (T)gload_f<float, NC>(io.w32, j);
         if constexpr (sizeof(T) == 8) return tload<T, NC>(reinterpret_cast<const T*>(io.w), j);
@@ -191,67 +281,71 @@ __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, i
     return (T)p.g_iso;
 }
 
-// Phase A for one warp tile: row sums of the rows that start and end in the
-// tile go through the epilogue; the tile's part of a first row that began
-// earlier goes to first[t]; the part of the row still open at the end goes
-// to agg[t].
-template <class T, class G, int GMODE, bool NC>
-__device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TileIO<T, G>& io, double& resid,
-                                          double& dang, WarpSmem<T>& ws) {
+// Phase A for one warp tile (nonzeros [t*PR_NZTILE, (t+1)*PR_NZTILE), lane l
+// owning PR_NZLANE consecutive ones).  Each lane gathers its values into
+// registers and finds its row boundaries in the row-end bitmap (a popc and a
+// shift, no search); rows ending in the tile are numbered in the compressed
+// list of non-empty rows from the tile's first row.  Per-lane segmented sums
+// go to shared memory, a warp scan joins rows split across lanes.  Rows that
+// start and end in the tile go through the epilogue; the tile's part of a
+// first row that began earlier goes to first[t]; the part of the row still
+// open at the end goes to agg[t].
+template <class T, class G, int GMODE, bool NC, bool LEAN>
+__device__ __forceinline__ void warp_tile(const PrParams& p, int t, uint32_t meta, const TileIO<T, G>& io,
+                                          Acc<T>& resid, Acc<T>& dang, WarpSmem<T>& ws) {
+    static_assert(PR_NZLANE == 8, "two 16-byte column loads per lane");
     const int lane = threadIdx.x & 31;
-    const int32_t i0 = __ldg(p.tile_i + t), k0 = __ldg(p.tile_k + t);
-    const int32_t i1 = __ldg(p.tile_i + t + 1), k1 = __ldg(p.tile_k + t + 1);
-    const int nA = i1 - i0, nB = k1 - k0;
-    const int32_t row0start = __ldg(p.row_ptr + i0);
+    const int rfirst = (int)(meta & 0x7fffffffu);
+    const int x_lo = (int)(meta >> 31);
+    const int kl = t * PR_NZTILE + lane * PR_NZLANE;
 
-    // ---- stage: column indices, then the gathers; row ends
-    int32_t cols[PR_WITEMS];
-#pragma unroll
-    for (int q = 0; q < PR_WITEMS; ++q) {
-        const int y = lane + 32 * q;
-        cols[q] = y < nB ? __ldg(p.col_idx + k0 + y) : 0;
+    // ---- every independent load of the tile at once.  The matrix arrays are
+    // read once per body: streaming loads (evict-first) keep them from
+    // pushing the gathered vector out of L2.
+    const int4* cp = reinterpret_cast<const int4*>(p.col_idx + kl);
+    const int4 ca = ld_stream(cp), cb = ld_stream(cp + 1);
+    const uint32_t myf = (ld_stream(p.rowend_bits + (kl >> 5)) >> (kl & 31)) & 0xffu;
+    const int nvalid = min(max(p.nnz - kl, 0), PR_NZLANE);
+    int pre_i = 0;
+    RowIn<T> pre;
+    pre.rold = (T)0;
+    pre.dd = (T)1;
+    pre.sinkword = 0;
+    if (rfirst + lane < p.n_ne) {
+        pre_i = ld_stream(p.ne_rows + rfirst + lane);
+        pre = row_inputs<T, G, NC, LEAN>(p, io, pre_i);
     }
+    const int cols[PR_NZLANE] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    T v[PR_NZLANE];
 #pragma unroll
-    for (int q = 0; q < PR_WITEMS; ++q) {
-        const int x = lane + 32 * q;
-        if (x < nA) ws.rowend[x] = __ldg(p.row_ptr + i0 + 1 + x);
-    }
-#pragma unroll
-    for (int q = 0; q < PR_WITEMS; ++q) {
-        const int y = lane + 32 * q;
-        if (y < nB) ws.val[y] = gather<T, G, GMODE, NC>(p, io, cols[q]);
-    }
-    __syncwarp();
+    for (int q = 0; q < PR_NZLANE; ++q) v[q] = q < nvalid ? gather<T, G, GMODE, NC>(p, io, cols[q]) : (T)0;
 
-    // ---- per-lane merge walk over PR_WITEMS items
-    const int total = nA + nB;
-    int d0 = lane * PR_WITEMS;
-    if (d0 > total) d0 = total;
-    int d1 = d0 + PR_WITEMS;
-    if (d1 > total) d1 = total;
-    int lo = d0 - nB > 0 ? d0 - nB : 0;
-    int hi = d0 < nA ? d0 : nA;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (ws.rowend[mid] <= k0 + (d0 - mid - 1)) lo = mid + 1;
-        else hi = mid;
+    // ---- row numbering: rows ending before this lane's nonzeros
+    const int cnt = __popc(myf);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(FULLMASK, incl, off);
+        if (lane >= off) incl += o;
     }
-    int x = lo, y = d0 - lo;
-    const int x_start = x;
+    const int before = incl - cnt;
+    const int nrows = __shfl_sync(FULLMASK, incl, 31);
+
+    // ---- per-lane segmented sums (row sums in ascending column order)
     T acc = (T)0;
-    for (int dd = d0; dd < d1; ++dd) {
-        if (x < nA && (y >= nB || ws.rowend[x] <= k0 + y)) {
-            ws.rowsum[x] = acc;
+    int idx = before;
+#pragma unroll
+    for (int q = 0; q < PR_NZLANE; ++q) {
+        acc += v[q];
+        if ((myf >> q) & 1u) {
+            ws.rowsum[idx] = acc;
+            ++idx;
             acc = (T)0;
-            ++x;
-        } else {
-            acc += ws.val[y];
-            ++y;
         }
     }
 
     // ---- warp segmented (reduce-by-key) scan of the lane carries
-    const int key = x;
+    const int key = idx;
     T val = acc;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -261,65 +355,99 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TileIO
     }
     const int exk = __shfl_up_sync(FULLMASK, key, 1);
     const T exv = __shfl_up_sync(FULLMASK, val, 1);
-    if (lane > 0 && x > x_start && exk == x_start) ws.rowsum[x_start] = exv + ws.rowsum[x_start];
-    if (lane == 31) p.agg[t] = (double)val;
+    if (lane > 0 && cnt > 0 && exk == before) ws.rowsum[before] = exv + ws.rowsum[before];
+    if (lane == 31) reinterpret_cast<T*>(p.agg)[t] = val;
     __syncwarp();
 
-    // ---- epilogue of the rows finished here
-    const int x_lo = (k0 > row0start) ? 1 : 0;
-    if (x_lo == 1 && nA > 0 && lane == 0) p.first[t] = (double)ws.rowsum[0];
-    for (int xr = x_lo + lane; xr < nA; xr += 32) {
-        const int32_t rs = xr == 0 ? row0start : ws.rowend[xr - 1];
-        row_epilogue<T, G, NC>(p, io, (int64_t)i0 + xr, ws.rowsum[xr], ws.rowend[xr] > rs, resid, dang);
+    // ---- epilogue of the rows finished here (row x on lane x % 32)
+    if (x_lo == 1 && nrows > 0 && lane == 0) reinterpret_cast<T*>(p.first)[t] = ws.rowsum[0];
+    if (lane >= x_lo && lane < nrows) row_epilogue<T, G, LEAN>(p, io, pre_i, ws.rowsum[lane], true, pre, resid, dang);
+    for (int x = 32 + lane; x < nrows; x += 32) {
+        const int i = ld_stream(p.ne_rows + rfirst + x);
+        const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, i);
+        row_epilogue<T, G, LEAN>(p, io, i, ws.rowsum[x], true, in, resid, dang);
     }
     __syncwarp();
+}
+
+// Rows without nonzeros: the epilogue with an empty sum.
+template <class T, class G, bool NC, bool LEAN>
+__device__ __forceinline__ void empty_rows(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
+    const int nthreads = gridDim.x * PR_BLOCK;
+    for (int e = blockIdx.x * PR_BLOCK + threadIdx.x; e < p.n_empty; e += nthreads) {
+        const int i = ld_stream(p.empty_rows + e);
+        const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, i);
+        row_epilogue<T, G, LEAN>(p, io, i, (T)0, false, in, resid, dang);
+    }
 }
 
 // Phase B: rows split across tiles.  Each thread takes tiles with a short
 // fixup (at most PR_LONG carries to add); each warp takes a long one.
-template <class T, class G, bool NC>
-__device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io, double& resid, double& dang) {
-    const int64_t nthreads = (int64_t)gridDim.x * PR_BLOCK;
-    for (int64_t t = (int64_t)blockIdx.x * PR_BLOCK + threadIdx.x; t < p.ntiles; t += nthreads) {
+template <class T, class G, bool NC, bool LEAN>
+__device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
+    const T* agg = reinterpret_cast<const T*>(p.agg);
+    const T* first = reinterpret_cast<const T*>(p.first);
+    const int nthreads = gridDim.x * PR_BLOCK;
+    for (int t = blockIdx.x * PR_BLOCK + threadIdx.x; t < p.ntiles; t += nthreads) {
         const FixDesc f = p.fix[t];
         if (f.row < 0 || t - f.ts > PR_LONG) continue;
-        double sum = 0.0;
-        for (int64_t tt = f.ts; tt < t; ++tt) sum += __ldcg(p.agg + tt);
-        sum += __ldcg(p.first + t);
-        row_epilogue<T, G, NC>(p, io, f.row, (T)sum, true, resid, dang);
+        const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, f.row);
+        T sum = (T)0;
+        for (int tt = f.ts; tt < t; ++tt) sum += __ldcg(agg + tt);
+        sum += __ldcg(first + t);
+        row_epilogue<T, G, LEAN>(p, io, f.row, sum, true, in, resid, dang);
     }
+    // rows spanning many tiles (hubs): one warp each, FP64 partial sums
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * NWARP;
-    for (int64_t q = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5); q < p.nlong; q += nwarps) {
+    const int nwarps = gridDim.x * NWARP;
+    for (int q = blockIdx.x * NWARP + (threadIdx.x >> 5); q < p.nlong; q += nwarps) {
         const int32_t t = p.longfix[q];
         const FixDesc f = p.fix[t];
         double sum = 0.0;
-        for (int64_t tt = f.ts + lane; tt < t; tt += 32) sum += __ldcg(p.agg + tt);
+        for (int tt = f.ts + lane; tt < t; tt += 32) sum += (double)__ldcg(agg + tt);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(FULLMASK, sum, off);
         if (lane == 0) {
-            sum += __ldcg(p.first + t);
-            row_epilogue<T, G, NC>(p, io, f.row, (T)sum, true, resid, dang);
+            sum += (double)__ldcg(first + t);
+            const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, f.row);
+            row_epilogue<T, G, LEAN>(p, io, f.row, (T)sum, true, in, resid, dang);
         }
     }
 }
 
+// Phase A over the tiles of this warp (static assignment, next tile's
+// coordinates prefetched).
+template <class T, class G, int GMODE, bool NC, bool LEAN>
+__device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                        Smem<T>& sm) {
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * NWARP;
+    int t = blockIdx.x * NWARP + warp;
+    uint32_t meta = t < p.ntiles ? __ldg(p.tile_meta + t) : 0u;
+    for (; t < p.ntiles; t += nwarps) {
+        const uint32_t nxt = t + nwarps < p.ntiles ? __ldg(p.tile_meta + t + nwarps) : 0u;
+        warp_tile<T, G, GMODE, NC, LEAN>(p, t, meta, io, resid, dang, sm.w[warp]);
+        meta = nxt;
+    }
+    empty_rows<T, G, NC, LEAN>(p, io, resid, dang);
+}
+
 template <class T>
 __device__ __forceinline__ T tele_value(const PrParams& p) {
-    return p.tele_from_slot ? (T)round_to(p.out.type, *p.tele_slot) : (T)0;
+    return p.tele_from_slot ? (T)round_to(p.out.type, *p.tele_slot) : (T)p.tele_const;
 }
 
 // One fused body per launch (also the fast unfused mxv): phase A, grid
-// barrier, phase B, then the last CTA folds the per-CTA partials.  In an
-// iterated sequence (p.iters_done != null) the launch first checks the loop
-// condition left by the previous launch and does nothing once it fails.
-template <class T, class G, int GMODE>
-__global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant__ PrParams p) {
+// barrier, phase B, then the last CTA folds the per-CTA partials.  LEAN
+// launches are bodies of an iterated sequence (a CUDA graph): each first
+// checks the loop condition left by the previous launch and does nothing
+// once it fails.
+template <class T, class G, int GMODE, bool LEAN>
+__global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const __grid_constant__ PrParams p) {
     __shared__ Smem<T> sm;
     __shared__ bool last;
-    const bool iterated = p.iters_done != nullptr;
     const int it = p.iter_index;
-    if (iterated) {
+    if (LEAN) {
         const double rd = it == 0 ? p.rdiff0 : *(volatile double*)p.resid_slot;
         const int64_t done_so_far = *(volatile int64_t*)p.iters_done;
         if (!(rd > p.tol) || done_so_far != it) return;
@@ -327,7 +455,7 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
     TileIO<T, G> io{};
     io.tele_scalar = p.tele_from_slot;
     io.tele = tele_value<T>(p);
-    if (iterated) {
+    if (LEAN) {
         io.r_old = reinterpret_cast<const T*>(it == 0 ? p.r0 : p.rbuf[(it - 1) & 1]);
         io.out = reinterpret_cast<T*>(p.rbuf[it & 1]);
         io.w = reinterpret_cast<const G*>(p.wbuf[it & 1]);
@@ -345,15 +473,12 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
     io.w32 = nullptr;
     io.w32_next = nullptr;
     io.phase32 = 0;
-    double resid = 0.0, dang = 0.0;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * NWARP;
-    for (int t = blockIdx.x * NWARP + warp; t < p.ntiles; t += nwarps)
-        warp_tile<T, G, GMODE, true>(p, t, io, resid, dang, sm.w[warp]);
+    Acc<T> racc, dacc;
+    phase_a<T, G, GMODE, true, LEAN>(p, io, racc, dacc, sm);
     if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
-    fixups<T, G, true>(p, io, resid, dang);
-    resid = block_sum_d<PR_BLOCK>(resid, sm.red);
-    dang = block_sum_d<PR_BLOCK>(dang, sm.red2);
+    fixups<T, G, true, LEAN>(p, io, racc, dacc);
+    const double resid = block_sum_d<PR_BLOCK>(racc.value(), sm.red);
+    const double dang = block_sum_d<PR_BLOCK>(dacc.value(), sm.red2);
     if (threadIdx.x == 0) {
         p.part[2 * blockIdx.x] = resid;
         p.part[2 * blockIdx.x + 1] = dang;
@@ -367,10 +492,10 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
     reduce_parts<T>(p.part, gridDim.x, R, D, sm);
     if (threadIdx.x == 0) {
         R = round_to(p.resid_type, R);
-        if (p.resid_slot && p.want_resid) *p.resid_slot = R;
+        if (p.resid_slot && (LEAN || p.want_resid)) *p.resid_slot = R;
         if (p.dang_slot && p.want_dang) *p.dang_slot = D;
         if (p.tele_slot && p.want_dang) *p.tele_slot = schain_apply(p.chain, D);
-        if (iterated) {
+        if (LEAN) {
             if (p.hist) p.hist[it] = R;
             *p.iters_done = it + 1;
         }
@@ -384,18 +509,16 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_iter_kernel(const __grid_constant
 // barrier, phase B, barrier, and every CTA folds the same partials in the
 // same order, so all CTAs take the same loop decision.
 template <class T, class G>
-__global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_constant__ PrParams p) {
+__global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_persistent_kernel(const __grid_constant__ PrParams p) {
     __shared__ Smem<T> sm;
     const int G_ = gridDim.x;
     const T* dd = reinterpret_cast<const T*>(p.dd);
     const T* r0 = reinterpret_cast<const T*>(p.r0);
     int phase32 = 0;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = G_ * NWARP;
 
     // prologue
     double dang = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += (int64_t)G_ * PR_BLOCK) {
+    for (int i = blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += G_ * PR_BLOCK) {
         const T rv = r0[i];
         const T q = rv / dd[i];
         if constexpr (sizeof(T) == 8) reinterpret_cast<double*>(p.wbuf[0])[i] = (double)q;
@@ -410,7 +533,7 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
     if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
     double R, D;
     reduce_parts<T>(p.part, G_, R, D, sm);
-    T tele = p.tele_from_slot ? (T)round_to(p.out.type, schain_apply(p.chain, D)) : (T)0;
+    T tele = p.tele_from_slot ? (T)round_to(p.out.type, schain_apply(p.chain, D)) : (T)p.tele_const;
     double rd = p.rdiff0;
     int it = 0;
     while (it < p.iters && rd > p.tol) {
@@ -421,18 +544,16 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
         io.w = reinterpret_cast<const G*>(p.wbuf[it & 1]);
         io.w_next = reinterpret_cast<G*>(p.wbuf[(it + 1) & 1]);
         io.w32 = reinterpret_cast<const float*>(p.wbuf32[it & 1]);
-        io.w32_next = phase32 ? reinterpret_cast<float*>(p.wbuf32[(it + 1) & 1]) : nullptr;
+        io.w32_next = reinterpret_cast<float*>(p.wbuf32[(it + 1) & 1]);
         io.phase32 = phase32;
         io.tele = tele;
-        io.tele_scalar = p.tele_from_slot;
-        double resid = 0.0;
-        dang = 0.0;
-        for (int t = blockIdx.x * NWARP + warp; t < p.ntiles; t += nwarps)
-            warp_tile<T, G, G_W, false>(p, t, io, resid, dang, sm.w[warp]);
+        io.tele_scalar = 1;
+        Acc<T> racc, dacc;
+        phase_a<T, G, G_W, false, true>(p, io, racc, dacc, sm);
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
-        fixups<T, G, false>(p, io, resid, dang);
-        resid = block_sum_d<PR_BLOCK>(resid, sm.red);
-        dang = block_sum_d<PR_BLOCK>(dang, sm.red2);
+        fixups<T, G, false, true>(p, io, racc, dacc);
+        const double resid = block_sum_d<PR_BLOCK>(racc.value(), sm.red);
+        dang = block_sum_d<PR_BLOCK>(dacc.value(), sm.red2);
         double* part = p.part + 2 * G_ * ((it + 1) & 1);
         if (threadIdx.x == 0) {
             part[2 * blockIdx.x] = resid;
@@ -449,7 +570,7 @@ __global__ void __launch_bounds__(PR_BLOCK) pr_persistent_kernel(const __grid_co
         if (p.mixed && !phase32 && rd < p.mixed_switch && it < p.iters && rd > p.tol) {
             const T* rcur = reinterpret_cast<const T*>(p.rbuf[(it - 1) & 1]);
             float* w32 = reinterpret_cast<float*>(p.wbuf32[it & 1]);
-            for (int64_t i = (int64_t)blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += (int64_t)G_ * PR_BLOCK)
+            for (int i = blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += G_ * PR_BLOCK)
                 w32[i] = (float)(__ldcg(rcur + i) / dd[i]);
             phase32 = 1;
             if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
@@ -495,43 +616,67 @@ int occupancy(K kernel) {
     return nb > 0 ? nb : 1;
 }
 
+// Kernel table: rank type x gather type x gather mode x (one body | whole
+// loop | body of an iterated sequence).
+template <class T, class G>
+struct Table {
+    static void* pick(int32_t gmode, int persistent, int lean) {
+        if (persistent) return (void*)pr_persistent_kernel<T, G>;
+        if (lean) return (void*)pr_iter_kernel<T, G, G_W, true>;
+        if (gmode == G_TD) return (void*)pr_iter_kernel<T, G, G_TD, false>;
+        if (gmode == G_ISO) return (void*)pr_iter_kernel<T, G, G_ISO, false>;
+        return (void*)pr_iter_kernel<T, G, G_W, false>;
+    }
+};
+
+void* pick_kernel_raw(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int lean) {
+    if (rank_type == GRB_FP64) return Table<double, double>::pick(gmode, persistent, lean);
+    if (rank_type != GRB_FP32) return nullptr;
+    if (gather_type == GRB_BF16) {
+        if (!persistent && !lean) return nullptr;   // BF16 gathers only in PageRank loops
+        return Table<float, __nv_bfloat16>::pick(gmode, persistent, lean);
+    }
+    return Table<float, float>::pick(gmode, persistent, lean);
+}
+
+void* pick_kernel(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int lean) {
+    void* k = pick_kernel_raw(rank_type, gather_type, gmode, persistent, lean);
+    // these kernels use little shared memory: give the rest to L1, which
+    // caches the gathered vector (a per-function hint, set before the
+    // occupancy query so that both see the same configuration)
+#if PR_MAX_L1
+    if (k) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
+#endif
+    return k;
+}
+
 }  // namespace
 
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent) {
-    if (rank_type == GRB_FP64) {
-        if (persistent) return occupancy(pr_persistent_kernel<double, double>);
-        if (gmode == G_TD) return occupancy(pr_iter_kernel<double, double, G_TD>);
-        if (gmode == G_ISO) return occupancy(pr_iter_kernel<double, double, G_ISO>);
-        return occupancy(pr_iter_kernel<double, double, G_W>);
-    }
-    if (gather_type == GRB_BF16) {
-        if (persistent) return occupancy(pr_persistent_kernel<float, __nv_bfloat16>);
-        return occupancy(pr_iter_kernel<float, __nv_bfloat16, G_W>);
-    }
-    if (persistent) return occupancy(pr_persistent_kernel<float, float>);
-    if (gmode == G_TD) return occupancy(pr_iter_kernel<float, float, G_TD>);
-    if (gmode == G_ISO) return occupancy(pr_iter_kernel<float, float, G_ISO>);
-    return occupancy(pr_iter_kernel<float, float, G_W>);
+    void* k = pick_kernel(rank_type, gather_type, gmode, persistent == 1, persistent == 2);
+    if (!k) return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, PR_BLOCK, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,
                       int persistent) {
-    if (rank_type == GRB_FP64) {
-        if (persistent) return coop_launch(pr_persistent_kernel<double, double>, grid, st, p);
-        if (p.gmode == G_TD) return coop_launch(pr_iter_kernel<double, double, G_TD>, grid, st, p);
-        if (p.gmode == G_ISO) return coop_launch(pr_iter_kernel<double, double, G_ISO>, grid, st, p);
-        return coop_launch(pr_iter_kernel<double, double, G_W>, grid, st, p);
-    }
-    if (rank_type != GRB_FP32) return cudaErrorInvalidValue;
-    if (gather_type == GRB_BF16) {
-        if (persistent) return coop_launch(pr_persistent_kernel<float, __nv_bfloat16>, grid, st, p);
-        if (p.gmode != G_W) return cudaErrorInvalidValue;
-        return coop_launch(pr_iter_kernel<float, __nv_bfloat16, G_W>, grid, st, p);
-    }
-    if (persistent) return coop_launch(pr_persistent_kernel<float, float>, grid, st, p);
-    if (p.gmode == G_TD) return coop_launch(pr_iter_kernel<float, float, G_TD>, grid, st, p);
-    if (p.gmode == G_ISO) return coop_launch(pr_iter_kernel<float, float, G_ISO>, grid, st, p);
-    return coop_launch(pr_iter_kernel<float, float, G_W>, grid, st, p);
+    // persistent: 0 = one body (planner), 1 = whole loop, 2 = body of an
+    // iterated sequence
+    void* k = pick_kernel(rank_type, gather_type, p.gmode, persistent == 1, persistent == 2);
+    if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(PR_BLOCK);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&p};
+    return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 cudaError_t launch_barrier_selftest(cudaStream_t st, SyncWords* sync, int32_t* status, int64_t spin_limit, int grid) {
