@@ -279,6 +279,34 @@ grb_info grb_iterate_end(grb_context ctx, grb_scalar cond, double tol, int64_t i
  * switched to the FP32 gather, 0 when it did not, -1 for other loops. */
 grb_info grb_iterate_history(grb_context ctx, double* hist, int64_t cap, int64_t* n, int32_t* mixed_phase);
 
+/* ------------------------------------------------ allocation-free call */
+
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory when they need a reduction -- code running while a
+ * stream is captured into a CUDA graph, code inside a host framework that
+ * owns the whole device memory budget, latency-critical paths that cannot
+ * pay for cudaMalloc's device synchronisation.
+ *
+ * *out = fold of the monoid over the n elements of the dense device array x
+ * (type INT32, FP32 or FP64), accumulated in FP64 in a fixed order (block b
+ * folds elements [4096*b, 4096*b+4096), then the block results in order).
+ * x and out are caller-owned device pointers; the call is asynchronous on
+ * `stream` (NULL = legacy default stream) and allocates nothing: its scratch
+ * (4096 partial sums and a counter, ~32 KB) is a fixed device array that
+ * every GPU loading the library keeps until the process exits.
+ *  - n may be at most GRB_NOALLOC_MAX_N; larger n returns GRB_INVALID_VALUE
+ *    before any GPU work.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (with that device current); make that first call before any stream
+ *    capture.
+ *  - All calls on a device share the scratch array: calls whose executions
+ *    overlap on the GPU (different streams, no ordering between them) race.
+ *  - Errors: GRB_NULL_POINTER, GRB_INVALID_VALUE (type, monoid or n),
+ *    GRB_DEVICE_ERROR (no device, or the launch failed). */
+#define GRB_NOALLOC_MAX_N 16777216ull
+grb_info grb_reduce_dense_noalloc(const void* x, grb_type type, uint64_t n, grb_monoid m, double* out,
+                                  void* stream);
+
 /* -------------------------------------------------------------- misc */
 
 /* Release any handle (sets *obj to NULL).  Pending work that other objects

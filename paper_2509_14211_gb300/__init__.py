@@ -116,6 +116,7 @@ def _declare(lib):
         "grb_free": [P(V)],
         "grb_error": [V],
         "grb_selftest_wait_timeout": [V, I64],
+        "grb_reduce_dense_noalloc": [V, I, U64, I, V, V],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -148,7 +149,7 @@ def symbols():
                         "grb_apply", "grb_apply_bind2nd", "grb_apply_bind2nd_scalar", "grb_assign_scalar",
                         "grb_mxv", "grb_ewise_add", "grb_ewise_mult", "grb_reduce", "grb_wait",
                         "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
-                        "grb_selftest_wait_timeout") if hasattr(lib, n)]
+                        "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc") if hasattr(lib, n)]
 
 
 def _check(rc: int, where: str, obj=None) -> int:
@@ -407,6 +408,24 @@ def grb_free(obj) -> None:
 
 def grb_error(obj) -> str:
     return (load().grb_error(obj) or b"").decode()
+
+
+GRB_NOALLOC_MAX_N = 16777216
+
+
+def grb_reduce_dense_noalloc(x, type_: int, n: int, monoid: int, out, stream=None) -> int:
+    """Allocation-free reduction of the dense device array `x` (torch CUDA
+    tensor or raw device pointer) into the one-double device buffer `out`,
+    asynchronously on `stream` (torch stream, raw handle, or None for
+    torch's current stream).  Returns the grb_info code (no exception, so
+    that callers can check the size limit themselves)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    xp = x if isinstance(x, int) else _ptr(x)
+    op = out if isinstance(out, int) else _ptr(out)
+    return load().grb_reduce_dense_noalloc(xp, int(type_), int(n), int(monoid), op, ctypes.c_void_p(handle))
 
 
 def grb_selftest_wait_timeout(ctx, spin_limit: int) -> int:
