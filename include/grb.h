@@ -148,6 +148,8 @@ typedef struct grb_stats {
     int64_t replayed_loops;     /* grb_iterate_end calls replayed from the host */
     int64_t device_bytes;       /* bytes currently held by the library */
     int64_t cache_hits;         /* signature-table hits (§III-C) */
+    int64_t last_loop_kernel_ns;/* device time of the last device loop's kernels
+                                   (CUDA events on the context stream) */
 } grb_stats;
 
 /* ------------------------------------------------------------ context */

@@ -60,7 +60,7 @@ class grb_binop(ctypes.Structure):
 class grb_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("kernel_launches", "fused_groups", "unfused_nodes",
                                               "elided_vectors", "persistent_loops", "replayed_loops",
-                                              "device_bytes", "cache_hits")]
+                                              "device_bytes", "cache_hits", "last_loop_kernel_ns")]
 
 
 def binop(code: int, k: float = 0.0) -> grb_binop:

@@ -218,6 +218,19 @@ struct PlanArgs {
     int32_t* counts;
 };
 cudaError_t build_row_plan(cudaStream_t st, const PlanArgs& a, AllocFn af, FreeFn ff, void* actx);
+
+// Vertex relabelling by descending degree (stable): new2old[k] = vertex
+// with the k-th largest degree, old2new its inverse (synchronises).
+cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t* new2old, int32_t* old2new,
+                         AllocFn af, FreeFn ff, void* actx);
+// COO (rows_out, cols_out) of A^T with both indices relabelled by old2new.
+cudaError_t launch_relabel_coo(cudaStream_t st, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                               const int32_t* old2new, int32_t* rows_out, int32_t* cols_out);
+// out[k] = in[perm[k]] for 4- or 8-byte elements.
+cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, const void* in, void* out, int32_t esize);
+// bit k of out = bit new2old[k] of in.
+cudaError_t launch_permute_bits(cudaStream_t st, int32_t n, const int32_t* new2old, const uint32_t* in_bits,
+                                uint32_t* out_bits);
 // Resident CTAs per SM of the fused kernel for the given rank / gather types.
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent);
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,

@@ -171,6 +171,54 @@ __global__ void tile_meta_kernel(int64_t ntiles, int32_t n_ne, const int32_t* __
     }
 }
 
+// ------------------------------------------------------- relabelling
+__global__ void iota_kernel(int32_t n, int32_t* v) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+
+__global__ void invert_perm_kernel(int32_t n, const int32_t* __restrict__ new2old, int32_t* old2new) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) old2new[new2old[k]] = k;
+}
+
+// COO of the relabelled A^T: nonzero (i, j) -> (old2new[i], old2new[j]);
+// one warp per row.
+__global__ void relabel_coo_kernel(int32_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                   const int32_t* __restrict__ old2new, int32_t* rows_out, int32_t* cols_out) {
+    const int lane = threadIdx.x & 31;
+    const int32_t nw = gridDim.x * (blockDim.x / 32);
+    for (int32_t i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int32_t ni = old2new[i];
+        for (int32_t k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
+            rows_out[k] = ni;
+            cols_out[k] = old2new[col_idx[k]];
+        }
+    }
+}
+
+__global__ void permute_gather_kernel(int32_t n, const int32_t* __restrict__ perm, const void* in, void* out,
+                                      int32_t esize) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int32_t s = perm[k];
+        if (esize == 8) static_cast<uint64_t*>(out)[k] = static_cast<const uint64_t*>(in)[s];
+        else static_cast<uint32_t*>(out)[k] = static_cast<const uint32_t*>(in)[s];
+    }
+}
+
+__global__ void permute_bits_kernel(int32_t n, const int32_t* __restrict__ new2old, const uint32_t* in_bits,
+                                    uint32_t* out_bits) {
+    const int32_t nw = (n + 31) / 32;
+    for (int32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        uint32_t b = 0;
+        for (int q = 0; q < 32; ++q) {
+            const int32_t k = w * 32 + q;
+            if (k >= n) break;
+            const int32_t o = new2old[k];
+            b |= ((in_bits[o >> 5] >> (o & 31)) & 1u) << q;
+        }
+        out_bits[w] = b;
+    }
+}
+
 inline int grid_for(int64_t n, int block = 256, int cap = 152 * 32) {
     int64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
@@ -323,6 +371,49 @@ cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* 
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || nrows <= 0) return e;
     nonempty_kernel<<<grid_for(nrows, 256, 152 * 8), 256, 0, st>>>(nrows, row_ptr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t* new2old, int32_t* old2new,
+                         AllocFn af, FreeFn ff, void* actx) {
+    Scratch S{af, ff, actx, {}};
+    cudaError_t e;
+    int32_t* ids = (int32_t*)S.get(sizeof(int32_t) * n);
+    int32_t* keys_out = (int32_t*)S.get(sizeof(int32_t) * n);
+    if (!ids || !keys_out) return cudaErrorMemoryAllocation;
+    iota_kernel<<<grid_for(n), 256, 0, st>>>(n, ids);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // stable descending sort by degree: ties keep ascending ids
+    size_t tb = 0;
+    if ((e = cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, deg, keys_out, ids, new2old, n, 0, 32, st)) !=
+        cudaSuccess)
+        return e;
+    void* tmp = S.get(tb);
+    if (!tmp) return cudaErrorMemoryAllocation;
+    if ((e = cub::DeviceRadixSort::SortPairsDescending(tmp, tb, deg, keys_out, ids, new2old, n, 0, 32, st)) !=
+        cudaSuccess)
+        return e;
+    invert_perm_kernel<<<grid_for(n), 256, 0, st>>>(n, new2old, old2new);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t launch_relabel_coo(cudaStream_t st, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                               const int32_t* old2new, int32_t* rows_out, int32_t* cols_out) {
+    relabel_coo_kernel<<<grid_for((int64_t)n * 32), 256, 0, st>>>(n, row_ptr, col_idx, old2new, rows_out, cols_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, const void* in, void* out, int32_t esize) {
+    if (n <= 0) return cudaSuccess;
+    permute_gather_kernel<<<grid_for(n), 256, 0, st>>>(n, perm, in, out, esize);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_bits(cudaStream_t st, int32_t n, const int32_t* new2old, const uint32_t* in_bits,
+                                uint32_t* out_bits) {
+    if (n <= 0) return cudaSuccess;
+    permute_bits_kernel<<<grid_for((n + 31) / 32), 256, 0, st>>>(n, new2old, in_bits, out_bits);
     return cudaGetLastError();
 }
 
