@@ -139,6 +139,7 @@ def run_profile_case(args):
         src, dst = new_id[src], new_id[dst]
     ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, args.loop_mode)
+    grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 0 if args.no_relabel else 1)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
@@ -175,6 +176,7 @@ def main():
     ap.add_argument("--loop-mode", type=int, default=1, help="1 persistent kernel, 2 CUDA graph of fused kernels")
     ap.add_argument("--unpermuted", action="store_true", help="profiling run on R-MAT without label scrambling")
     ap.add_argument("--degree-sorted", action="store_true", help="profiling run with vertices relabeled by out-degree")
+    ap.add_argument("--no-relabel", action="store_true", help="profiling run on the matrix in its input vertex order")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
@@ -261,6 +263,18 @@ def main():
     graph_ms = e0.elapsed_time(e1) / 3
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 1)
 
+    # the persistent loop on the matrix in its input vertex order
+    grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 0)
+    for _ in range(2):
+        P.run(-1.0, ITERS, "device")
+    e0.record(stream)
+    for _ in range(3):
+        P.run(-1.0, ITERS, "device")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    input_order_ms = e0.elapsed_time(e1) / 3
+    grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 1)
+
     # host loop with per-wait fusion (the paper's nonblocking mode)
     P.run(-1.0, 5, "host")
     e0.record(stream)
@@ -344,6 +358,10 @@ def main():
         "clocks": clocks,
         "fused_persistent_ms": ms,
         "fused_graph_ms": graph_ms,
+        "fused_persistent_input_order_ms": input_order_ms,
+        "vertex_order": ("device loops run on a copy of A^T with vertices numbered by descending out-degree, "
+                         "built once per matrix inside the library (cost in e2e); ranks are permuted in and out "
+                         "inside the timed step"),
         "fused_per_wait_host_loop_ms": perwait_ms,
         "unfused_op_by_op_ms": unfused_ms,
         "unfused_gpu_launches": unfused_launches,

@@ -255,6 +255,7 @@ grb_info grb_context_set(grb_context ctx, grb_option opt, int64_t value) {
             c->mixed_switch = (double)value * 1e-9;
             return GRB_SUCCESS;
         case GRB_OPT_MIXED: c->mixed = value != 0; return GRB_SUCCESS;
+        case GRB_OPT_RELABEL: c->relabel = value != 0; return GRB_SUCCESS;
     }
     return GRB_INVALID_VALUE;
 }

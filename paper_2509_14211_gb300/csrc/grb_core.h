@@ -60,6 +60,9 @@ struct Version {
     Node* producer = nullptr;  // non-null while pending
     // derived data cached on the version (immutable, so always valid)
     DevBuf sinkbits;       // bitmask of present entries (for sink vectors)
+    // copies in the vertex order of a relabelled matrix (key = its rel_id)
+    uint64_t perm_vals_key = 0, perm_bits_key = 0;
+    DevBuf perm_vals, perm_sinkbits;
 };
 
 enum class OpK : int {
@@ -117,6 +120,10 @@ struct Matrix {
     double iso_val = 1.0;
     int64_t nonempty_rows = -1;
     TilePlan* plan = nullptr;
+    // degree-ordered copy of a square pattern matrix for the device loops
+    Matrix* rel = nullptr;
+    DevBuf new2old, old2new;
+    uint64_t rel_id = 0;       // unique id of this relabelling
     std::string err;
 };
 
@@ -171,6 +178,7 @@ struct Ctx {
     int64_t spin_limit = int64_t(1) << 24;
     double mixed_switch = 1e-3;
     bool mixed = false;
+    bool relabel = true;  // device loops run on the degree-ordered copy of the matrix
     bool dry = false;     // replaying a loop body to inspect its DAG: never execute
     DevBuf red_scratch;   // per-block partials of the reduction kernels
     DevBuf red_counter;   // last-block counter of the reduction kernels
@@ -217,6 +225,8 @@ size_t type_size(grb_type t);
 grb_info cuda_check(Ctx* c, cudaError_t e, const char* what);
 grb_info ensure_plan(Ctx* c, Matrix* A);
 grb_info ensure_sinkbits(Ctx* c, Version* sinks);
+grb_info ensure_relabel(Ctx* c, Matrix* A);
+grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits);
 grb_info read_status(Ctx* c);
 PrParams plan_params_of(Ctx* c, Matrix* A);
 int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent);

@@ -179,6 +179,84 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
     return st;
 }
 
+// Degree-ordered copy of a square pattern matrix, built once and cached on
+// the matrix (matrices are immutable).  The gathers of the PageRank loop read
+// w[j] for the columns j of A^T; numbering vertices by descending out-degree
+// puts the most-gathered entries of w next to each other, so far fewer cache
+// lines serve the same gathers.  The loop's vectors are permuted into and out
+// of this order around the loop.
+grb_info ensure_relabel(Ctx* c, Matrix* A) {
+    if (A->rel) return GRB_SUCCESS;
+    if (A->nrows != A->ncols || A->vals.p || A->nrows <= 0) return GRB_INVALID_VALUE;
+    const int64_t n = A->nrows;
+    Matrix* R = new Matrix();
+    R->ctx = c;
+    R->type = A->type;
+    R->nrows = A->nrows;
+    R->ncols = A->ncols;
+    R->nnz = A->nnz;
+    R->iso_val = A->iso_val;
+    R->nonempty_rows = A->nonempty_rows;
+    R->row_ptr = buf_alloc(c, sizeof(int32_t) * (size_t)(n + 1));
+    R->col_idx = buf_alloc(c, sizeof(int32_t) * (size_t)padded_nnz(A->nnz));
+    DevBuf n2o = buf_alloc(c, sizeof(int32_t) * (size_t)n), o2n = buf_alloc(c, sizeof(int32_t) * (size_t)n);
+    grb_info st = (R->row_ptr.p && R->col_idx.p && n2o.p && o2n.p) ? GRB_SUCCESS : GRB_OUT_OF_MEMORY;
+    if (!st) {
+        RelabelArgs a;
+        a.n = (int32_t)n;
+        a.nnz = A->nnz;
+        a.row_ptr = (const int32_t*)A->row_ptr.p;
+        a.col_idx = (const int32_t*)A->col_idx.p;
+        a.new_row_ptr = (int32_t*)R->row_ptr.p;
+        a.new_col_idx = (int32_t*)R->col_idx.p;
+        a.new2old = (int32_t*)n2o.p;
+        a.old2new = (int32_t*)o2n.p;
+        st = cuda_check(c, relabel_csr(c->stream, a, [](void* x, size_t b) { return dev_alloc((Ctx*)x, b); },
+                                       [](void* x, void* q, size_t b) { dev_free((Ctx*)x, q, b); }, c),
+                        "relabel");
+        c->stats.kernel_launches += 9;
+    }
+    if (st) {
+        matrix_unref(R);
+        buf_free(c, n2o);
+        buf_free(c, o2n);
+        return st;
+    }
+    A->rel = R;
+    A->new2old = n2o;
+    A->old2new = o2n;
+    A->rel_id = c->next_id++;
+    return GRB_SUCCESS;
+}
+
+// A FULL vector's values (bits = false) or a sink bitmap (bits = true) in
+// the vertex order of A's relabelled copy, cached on the (immutable) version.
+grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits) {
+    const int32_t n = (int32_t)v->n;
+    const int32_t* n2o = (const int32_t*)A->new2old.p;
+    if (bits) {
+        if (v->perm_bits_key == A->rel_id && v->perm_sinkbits.p) return GRB_SUCCESS;
+        buf_free(c, v->perm_sinkbits);
+        v->perm_sinkbits = buf_alloc(c, sizeof(uint32_t) * (size_t)((n + 31) / 32));
+        if (!v->perm_sinkbits.p) return GRB_OUT_OF_MEMORY;
+        c->stats.kernel_launches++;
+        grb_info st = cuda_check(c, launch_permute_bits(c->stream, n, n2o, (const uint32_t*)v->sinkbits.p,
+                                                        (uint32_t*)v->perm_sinkbits.p), "permute sink bits");
+        if (!st) v->perm_bits_key = A->rel_id;
+        return st;
+    }
+    if (v->fmt != Fmt::FULL) return GRB_INVALID_VALUE;
+    if (v->perm_vals_key == A->rel_id && v->perm_vals.p) return GRB_SUCCESS;
+    buf_free(c, v->perm_vals);
+    v->perm_vals = buf_alloc(c, type_size(v->type) * (size_t)n);
+    if (!v->perm_vals.p) return GRB_OUT_OF_MEMORY;
+    c->stats.kernel_launches++;
+    grb_info st = cuda_check(c, launch_permute(c->stream, n, n2o, v->vals.p, v->perm_vals.p, (int32_t)type_size(v->type)),
+                             "permute vector");
+    if (!st) v->perm_vals_key = A->rel_id;
+    return st;
+}
+
 grb_info ensure_sinkbits(Ctx* c, Version* s) {
     if (s->sinkbits.p) return GRB_SUCCESS;
     s->sinkbits = buf_alloc(c, sizeof(uint32_t) * (size_t)((s->n + 31) / 32));

@@ -232,8 +232,19 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     const grb_type G = mixed ? GRB_BF16 : T;
     Matrix* A = lm.A;
     const int64_t n = A->nrows;
-    grb_info st = ensure_plan(c, A);
+    // AL: the matrix the loop kernels run on (A, or its degree-ordered copy;
+    // then every vector the kernels read or write is in that vertex order)
+    const bool rel = c->relabel;
+    grb_info st = GRB_SUCCESS;
+    Matrix* AL = A;
+    if (rel) {
+        st = ensure_relabel(c, A);
+        if (!st) AL = A->rel;
+    }
+    if (!st) st = ensure_plan(c, AL);
     if (!st && lm.uniform) st = ensure_sinkbits(c, lm.sinks);
+    if (!st && rel) st = ensure_perm_copy(c, A, lm.d, false);
+    if (!st && rel && lm.uniform) st = ensure_perm_copy(c, A, lm.sinks, true);
     if (st) return st;
     Version* r0 = lm.r->cur;
     ver_ref(r0);
@@ -270,19 +281,27 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
             st = cuda_check(c, launch_ewise(c->stream, n, e, w, o), "expand start vector");
         }
         r0data = r0full.p;
+    } else if (!st && rel) {
+        r0full = buf_alloc(c, tb);
+        if (!r0full.p) st = GRB_OUT_OF_MEMORY;
+        c->stats.kernel_launches++;
+        if (!st)
+            st = cuda_check(c, launch_permute(c->stream, (int32_t)n, (const int32_t*)A->new2old.p, r0->vals.p, r0full.p,
+                                              (int32_t)type_size(T)), "permute start vector");
+        r0data = r0full.p;
     }
     double* sl = (double*)slots.p;
     int64_t* iters_done = (int64_t*)(sl + 0);
     if (!st) st = cuda_check(c, cudaMemsetAsync(slots.p, 0, sizeof(double) * 8, c->stream), "loop slots");
 
-    PrParams p = plan_params_of(c, A);
+    PrParams p = plan_params_of(c, AL);
     p.gmode = G_W;
     p.has_base = 1;
     if (lm.uniform) {
         p.tele_from_slot = 1;
         p.tele_slot = sl + 3;
         p.want_dang = 1;
-        p.sinkbits = (const uint32_t*)lm.sinks->sinkbits.p;
+        p.sinkbits = (const uint32_t*)(rel ? lm.sinks->perm_sinkbits.p : lm.sinks->sinkbits.p);
         p.chain = lm.chain;
     } else {
         p.tele_from_slot = 0;
@@ -292,7 +311,7 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     p.resid_slot = sl + 1;
     p.resid_type = lm.resid_type;
     p.dang_slot = sl + 2;
-    p.dd = lm.d->vals.p;
+    p.dd = rel ? lm.d->perm_vals.p : lm.d->vals.p;
     p.out.type = T;
     p.out.full = 1;
     p.iters = iters;
@@ -316,13 +335,13 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     if (!st && cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess)
         cudaEventRecord(ev0, c->stream);
     if (!st && mode == 1) {
-        const int grid = pr_grid(c, A, T, G, G_W, 1);
+        const int grid = pr_grid(c, AL, T, G, G_W, 1);
         c->stats.kernel_launches++;
         st = cuda_check(c, launch_pr(c->stream, p, T, G, grid, 1), "persistent pagerank loop");
     } else if (!st) {
         // prologue (no bodies) + one fused kernel per body, as a CUDA graph
-        const int pgrid = pr_grid(c, A, T, G, G_W, 1);
-        const int igrid = pr_grid(c, A, T, G, G_W, 2);
+        const int pgrid = pr_grid(c, AL, T, G, G_W, 1);
+        const int igrid = pr_grid(c, AL, T, G, G_W, 2);
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         // capture on a private stream (the context's stream may be the
@@ -374,6 +393,20 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
             st = cuda_check(c, cudaMemcpy(c->last_hist.data(), hist.p, sizeof(double) * K, cudaMemcpyDeviceToHost), "history");
         c->last_mixed_phase = mixed ? (int)((int32_t*)(host_slots + 4))[0] : -1;
     }
+    // back to the caller's vertex order: out[i] = buf[old2new[i]]
+    auto unpermute = [&](DevBuf& b) -> grb_info {
+        if (!rel) return GRB_SUCCESS;
+        DevBuf o = buf_alloc(c, tb);
+        if (!o.p) return GRB_OUT_OF_MEMORY;
+        c->stats.kernel_launches++;
+        grb_info s2 = cuda_check(c, launch_permute(c->stream, (int32_t)n, (const int32_t*)A->old2new.p, b.p, o.p,
+                                                   (int32_t)type_size(T)), "unpermute rank");
+        buf_free(c, b);
+        b = o;
+        return s2;
+    };
+    if (!st && K >= 2) st = unpermute(rb[(K - 2) & 1]);
+    if (!st && K >= 1) st = unpermute(rb[(K - 1) & 1]);
     if (!st && K > 0) {
         // r_{K-1}: the start vector itself, or the other ping-pong buffer
         Version* rprev = r0;

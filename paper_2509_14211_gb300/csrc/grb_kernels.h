@@ -223,9 +223,22 @@ cudaError_t build_row_plan(cudaStream_t st, const PlanArgs& a, AllocFn af, FreeF
 // with the k-th largest degree, old2new its inverse (synchronises).
 cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t* new2old, int32_t* old2new,
                          AllocFn af, FreeFn ff, void* actx);
-// COO (rows_out, cols_out) of A^T with both indices relabelled by old2new.
-cudaError_t launch_relabel_coo(cudaStream_t st, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
-                               const int32_t* old2new, int32_t* rows_out, int32_t* cols_out);
+// Symmetric relabelling of a square pattern CSR matrix (A^T) by descending
+// column count (the out-degree of the graph): new row k = old row new2old[k]
+// with every column j renamed old2new[j], entries kept in their old order.
+// Outputs are preallocated: new_row_ptr[n+1], new_col_idx[padded_nnz(nnz)],
+// new2old[n], old2new[n].  Synchronises.
+struct RelabelArgs {
+    int32_t n;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    int32_t* new_row_ptr;
+    int32_t* new_col_idx;
+    int32_t* new2old;
+    int32_t* old2new;
+};
+cudaError_t relabel_csr(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx);
 // out[k] = in[perm[k]] for 4- or 8-byte elements.
 cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, const void* in, void* out, int32_t esize);
 // bit k of out = bit new2old[k] of in.

@@ -123,6 +123,8 @@ void ver_free_data(Version* v) {
     buf_free(c, v->present);
     buf_free(c, v->slot);
     buf_free(c, v->sinkbits);
+    buf_free(c, v->perm_vals);
+    buf_free(c, v->perm_sinkbits);
     if (v->iso_src) {
         Version* s = v->iso_src;
         v->iso_src = nullptr;
@@ -187,6 +189,9 @@ void matrix_unref(Matrix* A) {
         if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
         delete p;
     }
+    if (A->rel) matrix_unref(A->rel);
+    buf_free(c, A->new2old);
+    buf_free(c, A->old2new);
     A->kind = Kind::DEAD;
     delete A;
 }

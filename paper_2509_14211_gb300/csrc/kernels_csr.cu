@@ -180,18 +180,31 @@ __global__ void invert_perm_kernel(int32_t n, const int32_t* __restrict__ new2ol
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) old2new[new2old[k]] = k;
 }
 
-// COO of the relabelled A^T: nonzero (i, j) -> (old2new[i], old2new[j]);
-// one warp per row.
-__global__ void relabel_coo_kernel(int32_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                                   const int32_t* __restrict__ old2new, int32_t* rows_out, int32_t* cols_out) {
+// Row lengths of the relabelled A^T: new row k is old row new2old[k]
+// (len[n] = 0 so that an exclusive scan gives row_ptr[n] = nnz).
+__global__ void relabel_rowlen_kernel(int32_t n, const int32_t* __restrict__ row_ptr,
+                                      const int32_t* __restrict__ new2old, int32_t* len) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
+        if (k == n) {
+            len[k] = 0;
+        } else {
+            const int32_t o = new2old[k];
+            len[k] = row_ptr[o + 1] - row_ptr[o];
+        }
+    }
+}
+
+// Columns of the relabelled A^T, one warp per new row: the old row's
+// entries in their old order, each column renamed by old2new.
+__global__ void relabel_cols_kernel(int32_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                    const int32_t* __restrict__ new2old, const int32_t* __restrict__ old2new,
+                                    const int32_t* __restrict__ new_ptr, int32_t* new_col) {
     const int lane = threadIdx.x & 31;
     const int32_t nw = gridDim.x * (blockDim.x / 32);
-    for (int32_t i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); i < n; i += nw) {
-        const int32_t ni = old2new[i];
-        for (int32_t k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
-            rows_out[k] = ni;
-            cols_out[k] = old2new[col_idx[k]];
-        }
+    for (int32_t k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); k < n; k += nw) {
+        const int32_t o = new2old[k];
+        const int32_t b = row_ptr[o], len = row_ptr[o + 1] - b, nb = new_ptr[k];
+        for (int32_t q = lane; q < len; q += 32) new_col[nb + q] = old2new[col_idx[b + q]];
     }
 }
 
@@ -398,10 +411,29 @@ cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t launch_relabel_coo(cudaStream_t st, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
-                               const int32_t* old2new, int32_t* rows_out, int32_t* cols_out) {
-    relabel_coo_kernel<<<grid_for((int64_t)n * 32), 256, 0, st>>>(n, row_ptr, col_idx, old2new, rows_out, cols_out);
-    return cudaGetLastError();
+cudaError_t relabel_csr(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx) {
+    Scratch S{af, ff, actx, {}};
+    cudaError_t e;
+    const int32_t n = a.n;
+    int32_t* deg = (int32_t*)S.get(sizeof(int32_t) * (n + 1));
+    if (!deg) return cudaErrorMemoryAllocation;
+    if ((e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st)) != cudaSuccess) return e;
+    if (a.nnz > 0) col_count_kernel<<<grid_for(a.nnz), 256, 0, st>>>(a.nnz, a.col_idx, deg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = degree_order(st, n, deg, a.new2old, a.old2new, af, ff, actx)) != cudaSuccess) return e;
+    relabel_rowlen_kernel<<<grid_for(n + 1), 256, 0, st>>>(n, a.row_ptr, a.new2old, deg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    size_t tb = 0;
+    if ((e = cub::DeviceScan::ExclusiveSum(nullptr, tb, deg, a.new_row_ptr, n + 1, st)) != cudaSuccess) return e;
+    void* tmp = S.get(tb);
+    if (!tmp) return cudaErrorMemoryAllocation;
+    if ((e = cub::DeviceScan::ExclusiveSum(tmp, tb, deg, a.new_row_ptr, n + 1, st)) != cudaSuccess) return e;
+    // padding of the last tile: column 0, as in the CSR build
+    if ((e = cudaMemsetAsync(a.new_col_idx, 0, sizeof(int32_t) * padded_nnz(a.nnz), st)) != cudaSuccess) return e;
+    relabel_cols_kernel<<<grid_for((int64_t)n * 32), 256, 0, st>>>(n, a.row_ptr, a.col_idx, a.new2old, a.old2new,
+                                                                   a.new_row_ptr, a.new_col_idx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
 }
 
 cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, const void* in, void* out, int32_t esize) {

@@ -28,13 +28,14 @@ def grb():
 
 
 def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, persistent=0, fusion=True,
-         mixed=False):
+         mixed=False, relabel=True):
     from paper_2509_14211_gb300.pagerank import pagerank
 
     ctx = grb.grb_context_new(mode if mode is not None else grb.GRB_NONBLOCKING)
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, persistent)
     grb.grb_context_set(ctx, grb.GRB_OPT_FUSION, 1 if fusion else 0)
     grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 1 if mixed else 0)
+    grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 1 if relabel else 0)
     try:
         r, it = pagerank(ctx, n, src, dst, damping=D, tol=tol, itermax=itermax, rank_type=rank_type,
                          dangling=dangling, loop=loop)
@@ -53,16 +54,19 @@ def c0():
     return n, src, dst
 
 
-PATHS = [("device", 1, True, "nb"), ("device", 2, True, "nb"), ("host", 0, True, "nb"),
-         ("host", 0, False, "nb"), ("host", 0, True, "blocking")]
+# (loop, persistent option, fusion, mode, degree-ordered copy for device loops)
+PATHS = [("device", 1, True, "nb", True), ("device", 2, True, "nb", True), ("device", 1, True, "nb", False),
+         ("device", 2, True, "nb", False), ("host", 0, True, "nb", True), ("host", 0, False, "nb", True),
+         ("host", 0, True, "blocking", True)]
 
 
-@pytest.mark.parametrize("loop,persistent,fusion,mode", PATHS)
+@pytest.mark.parametrize("loop,persistent,fusion,mode,relabel", PATHS)
 @pytest.mark.parametrize("dangling", ["uniform", "gap"])
-def test_fp64_rmat10_all_paths(grb, c0, loop, persistent, fusion, mode, dangling):
+def test_fp64_rmat10_all_paths(grb, c0, loop, persistent, fusion, mode, relabel, dangling):
     n, src, dst = c0
     m = grb.GRB_BLOCKING if mode == "blocking" else grb.GRB_NONBLOCKING
-    r, it, stats, _ = _run(grb, n, src, dst, grb.GRB_FP64, dangling, loop, 1e-10, 100, m, persistent, fusion)
+    r, it, stats, _ = _run(grb, n, src, dst, grb.GRB_FP64, dangling, loop, 1e-10, 100, m, persistent, fusion,
+                           relabel=relabel)
     ref_conv, k_conv, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=1e-10, itermax=100, mode=dangling)
     assert abs(it - k_conv) <= 1
     ref, k, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=it, mode=dangling)
@@ -80,9 +84,9 @@ def test_fp32_fixed_iterations_scale16(grb, dangling):
     n = 1 << 16
     src, dst = graphgen.rmat_edges(16, 16, seed=1)
     ref, _, ref_hist = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=50, mode=dangling)
-    for persistent in (1, 2):
+    for persistent, relabel in ((1, True), (2, True), (1, False), (2, False)):
         r, it, _, (hist, _) = _run(grb, n, src, dst, grb.GRB_FP32, dangling, "device", -1.0, 50,
-                                   persistent=persistent)
+                                   persistent=persistent, relabel=relabel)
         assert it == 50
         assert np.sum(np.abs(r - ref)) <= 1e-6
         # FP32 ranks put a noise floor of ~n * eps32 * mean(r) ~ 1e-8 under
@@ -161,8 +165,8 @@ def test_edge_graphs(grb, case):
         dst = (rng.integers(0, n // 7, 40000) * 7).astype(np.int32)
     for rank_type, tol_ok in ((grb.GRB_FP64, 1e-12), (grb.GRB_FP32, 1e-6)):
         ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=15, mode="uniform")
-        for loop in ("device", "host"):
-            r, it, _, _ = _run(grb, n, src, dst, rank_type, "uniform", loop, -1.0, 15)
+        for loop, relabel in (("device", True), ("device", False), ("host", True)):
+            r, it, _, _ = _run(grb, n, src, dst, rank_type, "uniform", loop, -1.0, 15, relabel=relabel)
             assert it == 15
             err = np.max(np.abs(r - ref)) if rank_type == grb.GRB_FP64 else np.sum(np.abs(r - ref))
             assert err <= tol_ok, (case, loop, err)
