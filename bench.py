@@ -140,6 +140,8 @@ def run_profile_case(args):
     ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, args.loop_mode)
     grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 0 if args.no_relabel else 1)
+    if args.hot_bytes is not None:
+        grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, args.hot_bytes)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
@@ -155,6 +157,7 @@ def run_profile_case(args):
     ms = e0.elapsed_time(e1) / args.steps
     kms = grb.grb_context_stats(ctx)["last_loop_kernel_ns"] / 1e6
     print(json.dumps({"profile_case": True, "scale": args.scale, "n": n, "m": m, "iters": args.iters,
+                      "loop_mode": args.loop_mode, "relabel": not args.no_relabel, "hot_bytes": args.hot_bytes,
                       "ms_per_loop": ms, "kernel_ms": kms, "gteps": m * args.iters / (ms * 1e-3) / 1e9,
                       "kernel_gteps": m * args.iters / (kms * 1e-3) / 1e9}), flush=True)
     P.free()
@@ -177,6 +180,7 @@ def main():
     ap.add_argument("--unpermuted", action="store_true", help="profiling run on R-MAT without label scrambling")
     ap.add_argument("--degree-sorted", action="store_true", help="profiling run with vertices relabeled by out-degree")
     ap.add_argument("--no-relabel", action="store_true", help="profiling run on the matrix in its input vertex order")
+    ap.add_argument("--hot-bytes", type=int, default=None, help="profiling run: shared-memory hot copy size")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

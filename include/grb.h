@@ -124,13 +124,19 @@ typedef enum {
     GRB_OPT_MIXED = 5,         /* 1: FP32 PageRank loops gather the rank in BF16
                                   (FP32 accumulation) until the residual falls
                                   below the switch, then in FP32; 0 (default) off */
-    GRB_OPT_RELABEL = 6        /* 1 (default): device loops run on a copy of the
+    GRB_OPT_RELABEL = 6,       /* 1 (default): device loops run on a copy of the
                                   matrix with vertices numbered by descending
                                   out-degree (built once per matrix, cached; the
                                   loop's vectors are permuted in and out), so the
                                   rank gathers touch fewer cache lines; 0: the
                                   matrix as built */
+    GRB_OPT_HOT_BYTES = 7      /* bytes of shared memory per SM that the persistent
+                                  FP32 loop on a degree-ordered matrix uses for a
+                                  copy of the most-gathered rank entries
+                                  (0 .. GRB_HOT_BYTES_MAX; default 131072; 0 = off) */
 } grb_option;
+
+#define GRB_HOT_BYTES_MAX 196608
 
 /* Opaque handles. */
 typedef struct grb_context_s* grb_context;

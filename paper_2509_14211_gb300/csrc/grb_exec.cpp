@@ -293,10 +293,16 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
 
 PrParams plan_params_of(Ctx* c, Matrix* A) { return plan_params(c, A); }
 
-int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent) {
-    int g = pr_blocks_per_sm(T, G, gmode, persistent) * c->sm_count;
+int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n) {
+    int nb = pr_blocks_per_sm(T, G, gmode, persistent, hot_n);
+    if (nb <= 0) {
+        if (persistent == 1 && hot_n > 0) return 0;   // the hot-copy kernel cannot run: caller drops it
+        nb = 1;
+    }
+    int g = nb * c->sm_count;
     if (g > c->sm_count * 8) g = c->sm_count * 8;
-    const int64_t need = (A->plan->ntiles + PR_BLOCK / 32 - 1) / (PR_BLOCK / 32);   // one tile per warp at least
+    const int wpb = (persistent == 1 && hot_n > 0 ? PR_HOT_BLOCK : PR_BLOCK) / 32;
+    const int64_t need = (A->plan->ntiles + wpb - 1) / wpb;   // one tile per warp at least
     if (g > need) g = (int)need;
     return g < 1 ? 1 : g;
 }

@@ -335,7 +335,15 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     if (!st && cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess)
         cudaEventRecord(ev0, c->stream);
     if (!st && mode == 1) {
-        const int grid = pr_grid(c, AL, T, G, G_W, 1);
+        // shared-memory copy of the hottest entries of w: only useful when
+        // the vertices are in degree order
+        if (rel && !mixed && T == GRB_FP32 && c->hot_bytes >= 16)
+            p.hot_n = (int32_t)(std::min<int64_t>(n, c->hot_bytes / (int64_t)sizeof(float)) & ~(int64_t)3);
+        int grid = p.hot_n > 0 ? pr_grid(c, AL, T, G, G_W, 1, p.hot_n) : 0;
+        if (grid <= 0) {
+            p.hot_n = 0;
+            grid = pr_grid(c, AL, T, G, G_W, 1);
+        }
         c->stats.kernel_launches++;
         st = cuda_check(c, launch_pr(c->stream, p, T, G, grid, 1), "persistent pagerank loop");
     } else if (!st) {

@@ -166,6 +166,9 @@ struct PrParams {
     double mixed_switch = 1e-3;
     void* wbuf32[2] = {nullptr, nullptr};
     int32_t* mixed_phase = nullptr;  // 0 = BF16 gather, 1 = FP32 gather
+    // persistent loop: gathers of columns < hot_n are served from a copy of
+    // w[0, hot_n) in shared memory (multiple of 4; 0 = off; FP32 only)
+    int32_t hot_n = 0;
 };
 
 // --------------------------------------------------------------- launchers
@@ -244,8 +247,13 @@ cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, cons
 // bit k of out = bit new2old[k] of in.
 cudaError_t launch_permute_bits(cudaStream_t st, int32_t n, const int32_t* new2old, const uint32_t* in_bits,
                                 uint32_t* out_bits);
-// Resident CTAs per SM of the fused kernel for the given rank / gather types.
-int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent);
+// Resident CTAs per SM of the fused kernel for the given rank / gather types
+// (hot_n > 0: the persistent kernel with a hot copy of hot_n entries; 0 when
+// that configuration cannot run).
+int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n = 0);
+// Threads per CTA of the persistent kernel with the shared-memory hot copy
+// (one CTA per SM).
+constexpr int PR_HOT_BLOCK = 1024;
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,
                       int persistent);
 cudaError_t launch_barrier_selftest(cudaStream_t st, SyncWords* sync, int32_t* status, int64_t spin_limit, int grid);

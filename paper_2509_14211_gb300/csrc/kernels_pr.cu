@@ -67,11 +67,11 @@ struct WarpSmem {
     T rowsum[PR_NZTILE];   // sums of the rows ending in the warp's current tile
 };
 
-template <class T>
+template <class T, int NW = NWARP>
 struct Smem {
-    WarpSmem<T> w[NWARP];
-    double red[NWARP];
-    double red2[NWARP];
+    WarpSmem<T> w[NW];
+    double red[NW];
+    double red2[NW];
     double bc[2];
     int ok;
 };
@@ -150,15 +150,15 @@ __device__ bool grid_sync(SyncWords* s, int32_t* status, int64_t spin_limit, uin
 }
 
 // Deterministic fold of the per-CTA partials part[0..n) (pairs of doubles).
-template <class T>
-__device__ __forceinline__ void reduce_parts(const double* part, int n, double& a, double& b, Smem<T>& sm) {
+template <class T, int BLK = PR_BLOCK>
+__device__ __forceinline__ void reduce_parts(const double* part, int n, double& a, double& b, Smem<T, BLK / 32>& sm) {
     double x = 0.0, y = 0.0;
-    for (int c = threadIdx.x; c < n; c += PR_BLOCK) {
+    for (int c = threadIdx.x; c < n; c += BLK) {
         x += ld_relaxed_f64(part + 2 * c);
         y += ld_relaxed_f64(part + 2 * c + 1);
     }
-    x = block_sum_d<PR_BLOCK>(x, sm.red);
-    y = block_sum_d<PR_BLOCK>(y, sm.red2);
+    x = block_sum_d<BLK>(x, sm.red);
+    y = block_sum_d<BLK>(y, sm.red2);
     if (threadIdx.x == 0) { sm.bc[0] = x; sm.bc[1] = y; }
     __syncthreads();
     a = sm.bc[0];
@@ -205,6 +205,8 @@ struct TileIO {
     T tele;            // base value when it comes from a scalar
     int tele_scalar;   // 1: base = tele, 0: base from p.base
     int phase32;       // mixed precision: gather from w32
+    const G* hot;      // shared-memory copy of w[0, hot_n) (HOT kernels)
+    int hot_n;
 };
 
 // Epilogue inputs of one row, loaded ahead of use.
@@ -269,8 +271,11 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
     }
 }
 
-template <class T, class G, int GMODE, bool NC>
+template <class T, class G, int GMODE, bool NC, bool HOT = false>
 __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int j) {
+    if constexpr (HOT) {
+        if (j < io.hot_n) return (T)io.hot[j];
+    }
     if (GMODE == G_W) {
         if (io.phase32) return (T)gload_f<float, NC>(io.w32, j);
         if constexpr (sizeof(T) == 8) return tload<T, NC>(reinterpret_cast<const T*>(io.w), j);
@@ -290,35 +295,58 @@ __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, i
 // start and end in the tile go through the epilogue; the tile's part of a
 // first row that began earlier goes to first[t]; the part of the row still
 // open at the end goes to agg[t].
-template <class T, class G, int GMODE, bool NC, bool LEAN>
-__device__ __forceinline__ void warp_tile(const PrParams& p, int t, uint32_t meta, const TileIO<T, G>& io,
+// The loads that start a tile: its column indices, row-end bits and the
+// first row a lane finishes.  They depend only on the tile index (and the
+// tile's metadata), so a warp issues them one tile ahead and their memory
+// latency overlaps the current tile's gathers.
+struct TilePre {
+    uint32_t meta;
+    int4 ca, cb;
+    uint32_t bits;
+    int pre_i;   // -1: the lane finishes no row numbered rfirst + lane
+};
+
+__device__ __forceinline__ TilePre tile_pre(const PrParams& p, int t, uint32_t meta) {
+    // The matrix arrays are read once per body: streaming loads (evict-first)
+    // keep them from pushing the gathered vector out of L2.
+    const int lane = threadIdx.x & 31;
+    const int kl = t * PR_NZTILE + lane * PR_NZLANE;
+    TilePre f;
+    f.meta = meta;
+    const int4* cp = reinterpret_cast<const int4*>(p.col_idx + kl);
+    f.ca = ld_stream(cp);
+    f.cb = ld_stream(cp + 1);
+    f.bits = ld_stream(p.rowend_bits + (kl >> 5));
+    const int rfirst = (int)(meta & 0x7fffffffu);
+    f.pre_i = rfirst + lane < p.n_ne ? ld_stream(p.ne_rows + rfirst + lane) : -1;
+    return f;
+}
+
+template <class T, class G, int GMODE, bool NC, bool LEAN, bool HOT = false>
+__device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io,
                                           Acc<T>& resid, Acc<T>& dang, WarpSmem<T>& ws) {
     static_assert(PR_NZLANE == 8, "two 16-byte column loads per lane");
     const int lane = threadIdx.x & 31;
+    const uint32_t meta = f.meta;
     const int rfirst = (int)(meta & 0x7fffffffu);
     const int x_lo = (int)(meta >> 31);
     const int kl = t * PR_NZTILE + lane * PR_NZLANE;
-
-    // ---- every independent load of the tile at once.  The matrix arrays are
-    // read once per body: streaming loads (evict-first) keep them from
-    // pushing the gathered vector out of L2.
-    const int4* cp = reinterpret_cast<const int4*>(p.col_idx + kl);
-    const int4 ca = ld_stream(cp), cb = ld_stream(cp + 1);
-    const uint32_t myf = (ld_stream(p.rowend_bits + (kl >> 5)) >> (kl & 31)) & 0xffu;
+    const int4 ca = f.ca, cb = f.cb;
+    const uint32_t myf = (f.bits >> (kl & 31)) & 0xffu;
     const int nvalid = min(max(p.nnz - kl, 0), PR_NZLANE);
     int pre_i = 0;
     RowIn<T> pre;
     pre.rold = (T)0;
     pre.dd = (T)1;
     pre.sinkword = 0;
-    if (rfirst + lane < p.n_ne) {
-        pre_i = ld_stream(p.ne_rows + rfirst + lane);
+    if (f.pre_i >= 0) {
+        pre_i = f.pre_i;
         pre = row_inputs<T, G, NC, LEAN>(p, io, pre_i);
     }
     const int cols[PR_NZLANE] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
     T v[PR_NZLANE];
 #pragma unroll
-    for (int q = 0; q < PR_NZLANE; ++q) v[q] = q < nvalid ? gather<T, G, GMODE, NC>(p, io, cols[q]) : (T)0;
+    for (int q = 0; q < PR_NZLANE; ++q) v[q] = q < nvalid ? gather<T, G, GMODE, NC, HOT>(p, io, cols[q]) : (T)0;
 
     // ---- row numbering: rows ending before this lane's nonzeros
     const int cnt = __popc(myf);
@@ -373,8 +401,8 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, uint32_t met
 // Rows without nonzeros: the epilogue with an empty sum.
 template <class T, class G, bool NC, bool LEAN>
 __device__ __forceinline__ void empty_rows(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
-    const int nthreads = gridDim.x * PR_BLOCK;
-    for (int e = blockIdx.x * PR_BLOCK + threadIdx.x; e < p.n_empty; e += nthreads) {
+    const int nthreads = gridDim.x * blockDim.x;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.n_empty; e += nthreads) {
         const int i = ld_stream(p.empty_rows + e);
         const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, i);
         row_epilogue<T, G, LEAN>(p, io, i, (T)0, false, in, resid, dang);
@@ -387,8 +415,8 @@ template <class T, class G, bool NC, bool LEAN>
 __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
     const T* agg = reinterpret_cast<const T*>(p.agg);
     const T* first = reinterpret_cast<const T*>(p.first);
-    const int nthreads = gridDim.x * PR_BLOCK;
-    for (int t = blockIdx.x * PR_BLOCK + threadIdx.x; t < p.ntiles; t += nthreads) {
+    const int nthreads = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p.ntiles; t += nthreads) {
         const FixDesc f = p.fix[t];
         if (f.row < 0 || t - f.ts > PR_LONG) continue;
         const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, f.row);
@@ -399,8 +427,9 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
     }
     // rows spanning many tiles (hubs): one warp each, FP64 partial sums
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * NWARP;
-    for (int q = blockIdx.x * NWARP + (threadIdx.x >> 5); q < p.nlong; q += nwarps) {
+    const int bw = blockDim.x >> 5;
+    const int nwarps = gridDim.x * bw;
+    for (int q = blockIdx.x * bw + (threadIdx.x >> 5); q < p.nlong; q += nwarps) {
         const int32_t t = p.longfix[q];
         const FixDesc f = p.fix[t];
         double sum = 0.0;
@@ -417,17 +446,26 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
 
 // Phase A over the tiles of this warp (static assignment, next tile's
 // coordinates prefetched).
-template <class T, class G, int GMODE, bool NC, bool LEAN>
+template <class T, class G, int GMODE, bool NC, bool LEAN, bool HOT = false, int NW = NWARP>
 __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
-                                        Smem<T>& sm) {
+                                        Smem<T, NW>& sm) {
     const int warp = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * NWARP;
-    int t = blockIdx.x * NWARP + warp;
-    uint32_t meta = t < p.ntiles ? __ldg(p.tile_meta + t) : 0u;
+    const int nwarps = gridDim.x * NW;
+    int t = blockIdx.x * NW + warp;
+    // software pipeline: the metadata two tiles ahead, the tile-start loads
+    // one tile ahead
+    uint32_t meta2 = t + nwarps < p.ntiles ? __ldg(p.tile_meta + t + nwarps) : 0u;
+    TilePre f;
+    if (t < p.ntiles) f = tile_pre(p, t, __ldg(p.tile_meta + t));
     for (; t < p.ntiles; t += nwarps) {
-        const uint32_t nxt = t + nwarps < p.ntiles ? __ldg(p.tile_meta + t + nwarps) : 0u;
-        warp_tile<T, G, GMODE, NC, LEAN>(p, t, meta, io, resid, dang, sm.w[warp]);
-        meta = nxt;
+        const TilePre cur = f;
+        const int t1 = t + nwarps;
+        if (t1 < p.ntiles) {
+            const uint32_t m1 = meta2;
+            meta2 = t1 + nwarps < p.ntiles ? __ldg(p.tile_meta + t1 + nwarps) : 0u;
+            f = tile_pre(p, t1, m1);
+        }
+        warp_tile<T, G, GMODE, NC, LEAN, HOT>(p, t, cur, io, resid, dang, sm.w[warp]);
     }
     empty_rows<T, G, NC, LEAN>(p, io, resid, dang);
 }
@@ -508,9 +546,18 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 // r_0), then bodies while the condition holds; each body is phase A,
 // barrier, phase B, barrier, and every CTA folds the same partials in the
 // same order, so all CTAs take the same loop decision.
-template <class T, class G>
-__global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_persistent_kernel(const __grid_constant__ PrParams p) {
-    __shared__ Smem<T> sm;
+//
+// HOT (one CTA of BLK = 1024 threads per SM): at the start of each body the
+// CTA copies w[0, hot_n) into shared memory and serves gathers of those
+// columns from there.  With vertices numbered by descending out-degree these
+// are the most-gathered entries (for R-MAT, the first 32K of 4M vertices
+// take about half of all gathers), so half of the random gathers never reach
+// L1/L2; the copy costs hot_n words per CTA per body from L2.
+template <class T, class G, int BLK, bool HOT>
+__global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
+    pr_persistent_kernel(const __grid_constant__ PrParams p) {
+    __shared__ Smem<T, BLK / 32> sm;
+    extern __shared__ int4 hot_raw[];
     const int G_ = gridDim.x;
     const T* dd = reinterpret_cast<const T*>(p.dd);
     const T* r0 = reinterpret_cast<const T*>(p.r0);
@@ -518,21 +565,21 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_persistent_kernel(c
 
     // prologue
     double dang = 0.0;
-    for (int i = blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += G_ * PR_BLOCK) {
+    for (int i = blockIdx.x * BLK + threadIdx.x; i < p.nrows; i += G_ * BLK) {
         const T rv = r0[i];
         const T q = rv / dd[i];
         if constexpr (sizeof(T) == 8) reinterpret_cast<double*>(p.wbuf[0])[i] = (double)q;
         else gstore<G>(reinterpret_cast<G*>(p.wbuf[0]), i, (float)q);
         if (p.want_dang && ((p.sinkbits[i >> 5] >> (i & 31)) & 1u)) dang += (double)rv;
     }
-    dang = block_sum_d<PR_BLOCK>(dang, sm.red2);
+    dang = block_sum_d<BLK>(dang, sm.red2);
     if (threadIdx.x == 0) {
         p.part[2 * blockIdx.x] = 0.0;
         p.part[2 * blockIdx.x + 1] = dang;
     }
     if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
     double R, D;
-    reduce_parts<T>(p.part, G_, R, D, sm);
+    reduce_parts<T, BLK>(p.part, G_, R, D, sm);
     T tele = p.tele_from_slot ? (T)round_to(p.out.type, schain_apply(p.chain, D)) : (T)p.tele_const;
     double rd = p.rdiff0;
     int it = 0;
@@ -548,19 +595,28 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_persistent_kernel(c
         io.phase32 = phase32;
         io.tele = tele;
         io.tele_scalar = 1;
+        io.hot = reinterpret_cast<const G*>(hot_raw);
+        io.hot_n = HOT ? p.hot_n : 0;
+        if constexpr (HOT) {
+            // w of this body was written before the last grid barrier
+            const int4* src = reinterpret_cast<const int4*>(io.w);
+            const int nvec = (int)(((int64_t)p.hot_n * (int64_t)sizeof(G)) / 16);
+            for (int k = threadIdx.x; k < nvec; k += BLK) hot_raw[k] = __ldcg(src + k);
+            __syncthreads();
+        }
         Acc<T> racc, dacc;
-        phase_a<T, G, G_W, false, true>(p, io, racc, dacc, sm);
+        phase_a<T, G, G_W, false, true, HOT, BLK / 32>(p, io, racc, dacc, sm);
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
         fixups<T, G, false, true>(p, io, racc, dacc);
-        const double resid = block_sum_d<PR_BLOCK>(racc.value(), sm.red);
-        dang = block_sum_d<PR_BLOCK>(dacc.value(), sm.red2);
+        const double resid = block_sum_d<BLK>(racc.value(), sm.red);
+        dang = block_sum_d<BLK>(dacc.value(), sm.red2);
         double* part = p.part + 2 * G_ * ((it + 1) & 1);
         if (threadIdx.x == 0) {
             part[2 * blockIdx.x] = resid;
             part[2 * blockIdx.x + 1] = dang;
         }
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
-        reduce_parts<T>(part, G_, R, D, sm);
+        reduce_parts<T, BLK>(part, G_, R, D, sm);
         rd = round_to(p.resid_type, R);
         if (p.tele_from_slot) tele = (T)round_to(p.out.type, schain_apply(p.chain, D));
         if (blockIdx.x == 0 && threadIdx.x == 0 && p.hist) p.hist[it] = rd;
@@ -570,7 +626,7 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_persistent_kernel(c
         if (p.mixed && !phase32 && rd < p.mixed_switch && it < p.iters && rd > p.tol) {
             const T* rcur = reinterpret_cast<const T*>(p.rbuf[(it - 1) & 1]);
             float* w32 = reinterpret_cast<float*>(p.wbuf32[it & 1]);
-            for (int i = blockIdx.x * PR_BLOCK + threadIdx.x; i < p.nrows; i += G_ * PR_BLOCK)
+            for (int i = blockIdx.x * BLK + threadIdx.x; i < p.nrows; i += G_ * BLK)
                 w32[i] = (float)(__ldcg(rcur + i) / dd[i]);
             phase32 = 1;
             if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
@@ -621,7 +677,7 @@ int occupancy(K kernel) {
 template <class T, class G>
 struct Table {
     static void* pick(int32_t gmode, int persistent, int lean) {
-        if (persistent) return (void*)pr_persistent_kernel<T, G>;
+        if (persistent) return (void*)pr_persistent_kernel<T, G, PR_BLOCK, false>;
         if (lean) return (void*)pr_iter_kernel<T, G, G_W, true>;
         if (gmode == G_TD) return (void*)pr_iter_kernel<T, G, G_TD, false>;
         if (gmode == G_ISO) return (void*)pr_iter_kernel<T, G, G_ISO, false>;
@@ -650,25 +706,49 @@ void* pick_kernel(int32_t rank_type, int32_t gather_type, int32_t gmode, int per
     return k;
 }
 
+// The persistent loop with the shared-memory copy of the hottest gathered
+// entries: FP32 ranks and gathers only (the FP64 kernel's row-sum slices for
+// 32 warps would exceed the static shared-memory limit).
+void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn) {
+    if (rank_type != GRB_FP32 || gather_type != GRB_FP32) return nullptr;
+    void* k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) return nullptr;
+    return k;
+}
+
 }  // namespace
 
-int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent) {
-    void* k = pick_kernel(rank_type, gather_type, gmode, persistent == 1, persistent == 2);
-    if (!k) return 1;
+int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n) {
+    int block = PR_BLOCK;
+    size_t dyn = 0;
+    void* k = nullptr;
+    if (persistent == 1 && hot_n > 0) {
+        dyn = (size_t)hot_n * sizeof(float);
+        block = PR_HOT_BLOCK;
+        k = pick_hot(rank_type, gather_type, dyn);
+    } else {
+        k = pick_kernel(rank_type, gather_type, gmode, persistent == 1, persistent == 2);
+    }
+    if (!k) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, PR_BLOCK, 0) != cudaSuccess) return 1;
-    return nb > 0 ? nb : 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, dyn) != cudaSuccess) return 0;
+    return nb;
 }
 
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,
                       int persistent) {
     // persistent: 0 = one body (planner), 1 = whole loop, 2 = body of an
     // iterated sequence
-    void* k = pick_kernel(rank_type, gather_type, p.gmode, persistent == 1, persistent == 2);
+    const bool hot = persistent == 1 && p.hot_n > 0;
+    if (hot && (p.hot_n % 4 != 0 || p.hot_n > p.nrows || p.mixed)) return cudaErrorInvalidValue;
+    const size_t dyn = hot ? (size_t)p.hot_n * sizeof(float) : 0;
+    void* k = hot ? pick_hot(rank_type, gather_type, dyn)
+                  : pick_kernel(rank_type, gather_type, p.gmode, persistent == 1, persistent == 2);
     if (!k) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(PR_BLOCK);
+    cfg.blockDim = dim3(hot ? PR_HOT_BLOCK : PR_BLOCK);
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

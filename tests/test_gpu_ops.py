@@ -282,6 +282,11 @@ def test_api_errors_are_immediate(grb, ctx):
     assert e.value.code == grb.GRB_DOMAIN_MISMATCH
     for h in (v, u, i):
         grb.grb_free(h)
+    for opt, bad in ((grb.GRB_OPT_HOT_BYTES, -1), (grb.GRB_OPT_HOT_BYTES, grb.GRB_HOT_BYTES_MAX + 1),
+                     (grb.GRB_OPT_PERSISTENT, 4), (grb.GRB_OPT_SPIN_LIMIT, 0), (99, 1)):
+        with pytest.raises(grb.GrbError) as e:
+            grb.grb_context_set(ctx, opt, bad)
+        assert e.value.code == grb.GRB_INVALID_VALUE
 
 
 def test_device_wait_timeout_is_reported_not_hung(grb, ctx):

@@ -28,7 +28,7 @@ def grb():
 
 
 def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, persistent=0, fusion=True,
-         mixed=False, relabel=True):
+         mixed=False, relabel=True, hot_bytes=None):
     from paper_2509_14211_gb300.pagerank import pagerank
 
     ctx = grb.grb_context_new(mode if mode is not None else grb.GRB_NONBLOCKING)
@@ -36,6 +36,8 @@ def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, p
     grb.grb_context_set(ctx, grb.GRB_OPT_FUSION, 1 if fusion else 0)
     grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 1 if mixed else 0)
     grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 1 if relabel else 0)
+    if hot_bytes is not None:
+        grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, hot_bytes)
     try:
         r, it = pagerank(ctx, n, src, dst, damping=D, tol=tol, itermax=itermax, rank_type=rank_type,
                          dangling=dangling, loop=loop)
@@ -84,9 +86,14 @@ def test_fp32_fixed_iterations_scale16(grb, dangling):
     n = 1 << 16
     src, dst = graphgen.rmat_edges(16, 16, seed=1)
     ref, _, ref_hist = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=50, mode=dangling)
-    for persistent, relabel in ((1, True), (2, True), (1, False), (2, False)):
+    # persistent kernel with the default, no, a partial-warp-sized and the
+    # largest shared-memory hot copy (n = 65536: the largest covers 3/4 of
+    # the vertices); the CUDA-graph loop; both on the input vertex order
+    for persistent, relabel, hot in ((1, True, None), (1, True, 0), (1, True, 1040),
+                                     (1, True, grb.GRB_HOT_BYTES_MAX), (2, True, None), (1, False, None),
+                                     (2, False, None)):
         r, it, _, (hist, _) = _run(grb, n, src, dst, grb.GRB_FP32, dangling, "device", -1.0, 50,
-                                   persistent=persistent, relabel=relabel)
+                                   persistent=persistent, relabel=relabel, hot_bytes=hot)
         assert it == 50
         assert np.sum(np.abs(r - ref)) <= 1e-6
         # FP32 ranks put a noise floor of ~n * eps32 * mean(r) ~ 1e-8 under
