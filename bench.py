@@ -131,7 +131,10 @@ def run_profile_case(args):
 
     torch.cuda.set_device(0)
     n = 1 << args.scale
-    src, dst = graphgen.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED, permute=not args.unpermuted)
+    if args.graph == "er":
+        src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
+    else:
+        src, dst = graphgen.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED, permute=not args.unpermuted)
     if args.degree_sorted:   # relabel by descending out-degree (host side, for the experiment)
         order = np.argsort(-np.bincount(src, minlength=n), kind="stable")
         new_id = np.empty(n, dtype=np.int32)
@@ -142,27 +145,76 @@ def run_profile_case(args):
     grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 0 if args.no_relabel else 1)
     if args.hot_bytes is not None:
         grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, args.hot_bytes)
+    grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 1 if args.mixed else 0)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
     for _ in range(args.warmup):
-        P.run(-1.0, args.iters, "device")
+        P.run(args.tol, args.iters, "device")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
+    done = 0
     for _ in range(args.steps):
-        P.run(-1.0, args.iters, "device")
+        done = P.run(args.tol, args.iters, "device")
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     kms = grb.grb_context_stats(ctx)["last_loop_kernel_ns"] / 1e6
-    print(json.dumps({"profile_case": True, "scale": args.scale, "n": n, "m": m, "iters": args.iters,
+    print(json.dumps({"profile_case": True, "graph": args.graph, "mixed": args.mixed, "scale": args.scale, "n": n,
+                      "m": m, "iters": done,
                       "loop_mode": args.loop_mode, "relabel": not args.no_relabel, "hot_bytes": args.hot_bytes,
-                      "ms_per_loop": ms, "kernel_ms": kms, "gteps": m * args.iters / (ms * 1e-3) / 1e9,
-                      "kernel_gteps": m * args.iters / (kms * 1e-3) / 1e9}), flush=True)
+                      "ms_per_loop": ms, "kernel_ms": kms, "gteps": m * done / (ms * 1e-3) / 1e9,
+                      "kernel_gteps": m * done / (kms * 1e-3) / 1e9}), flush=True)
     P.free()
     grb.grb_free(AT)
     grb.grb_free(ctx)
+
+
+MIXED_N_LOG2, MIXED_TOL = 24, 1e-6 * (1 - DAMPING) / DAMPING
+
+
+def run_mixed_leg(grb, torch, stream):
+    """Mixed precision on Erdos-Renyi 2^24 (out-degree 16, 2% sinks, seed 2):
+    BF16 gathers until the residual falls below 1e-3 (or stalls), then FP32,
+    to an L1 change of 1e-6 (1-d)/d; beside it the FP32-only loop to the same
+    stop.  Times are CUDA events around grb_iterate_end (graph resident)."""
+    import graphgen
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
+
+    n = 1 << MIXED_N_LOG2
+    src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 1)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    del src, dst
+    m = grb.grb_matrix_nvals(AT)
+    P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+    out = {"workload": "Erdos-Renyi 2^24 vertices, out-degree 16, 2% sinks, seed 2, uniform dangling",
+           "n": n, "m": m, "stop_l1_change": MIXED_TOL}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for mixed in (1, 0):
+        grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, mixed)
+        P.run(MIXED_TOL, 500, "device")          # warm-up (builds plans, sink bits)
+        times, iters = [], 0
+        for _ in range(3):
+            e0.record(stream)
+            iters = P.run(MIXED_TOL, 500, "device")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        hist, phase = grb.grb_iterate_history(ctx)
+        r = P.rank().astype(np.float64)
+        ms = sorted(times)[1]
+        key = "mixed_bf16_fp32" if mixed else "fp32_only"
+        out[key] = {"ms": ms, "iterations": int(iters), "gteps": m * iters / (ms * 1e-3) / 1e9,
+                    "final_l1_change": float(hist[-1]), "switched_to_fp32": bool(phase == 1) if mixed else None,
+                    "rank_sum": float(np.sum(r)), "rank_min": float(np.min(r))}
+    out["mixed_speedup"] = out["fp32_only"]["ms"] / out["mixed_bf16_fp32"]["ms"]
+    P.free()
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+    return out
 
 
 def main():
@@ -172,6 +224,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the FP64 oracle (error and CPU baseline)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision Erdos-Renyi 2^24 leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="profiling run: only the fused device loop, on --scale/--iters (no JSON contract)")
     ap.add_argument("--scale", type=int, default=SCALE)
@@ -181,6 +234,9 @@ def main():
     ap.add_argument("--degree-sorted", action="store_true", help="profiling run with vertices relabeled by out-degree")
     ap.add_argument("--no-relabel", action="store_true", help="profiling run on the matrix in its input vertex order")
     ap.add_argument("--hot-bytes", type=int, default=None, help="profiling run: shared-memory hot copy size")
+    ap.add_argument("--graph", default="rmat", choices=["rmat", "er"], help="profiling run: graph family")
+    ap.add_argument("--mixed", action="store_true", help="profiling run: BF16 gather, then FP32")
+    ap.add_argument("--tol", type=float, default=-1.0, help="profiling run: stop at this L1 change")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
@@ -333,6 +389,8 @@ def main():
     grb.grb_free(AT)
     grb.grb_free(ctx)
 
+    mixed_leg = run_mixed_leg(grb, torch, stream) if not args.no_mixed else None
+
     # ---------------------------------------------------------- roofline
     # algorithmic bytes of one launch of the persistent kernel: per body
     # 4(n+1) row_ptr + 4m col_idx + 4n w gathered once + 4n d + 4n r_old +
@@ -371,6 +429,7 @@ def main():
         "unfused_gpu_launches": unfused_launches,
         "fused_vs_unfused": unfused_ms / ms,
         "residual_after_50": rdiff,
+        "mixed_er24": mixed_leg,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and not args.no_oracle:

@@ -124,6 +124,7 @@ struct Matrix {
     Matrix* rel = nullptr;
     DevBuf new2old, old2new;
     uint64_t rel_id = 0;       // unique id of this relabelling
+    bool rel_checked = false;  // the degree order was examined (rel null: not worth it)
     std::string err;
 };
 

@@ -184,45 +184,69 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
 // w[j] for the columns j of A^T; numbering vertices by descending out-degree
 // puts the most-gathered entries of w next to each other, so far fewer cache
 // lines serve the same gathers.  The loop's vectors are permuted into and out
-// of this order around the loop.
+// of this order around the loop.  On graphs without hubs (the REL_TOP
+// vertices of largest out-degree carry less than REL_MIN_COVER of the edges)
+// the order buys nothing and no copy is made: A->rel stays null.
+static constexpr int32_t REL_TOP = 32768;
+static constexpr double REL_MIN_COVER = 0.10;
+
 grb_info ensure_relabel(Ctx* c, Matrix* A) {
-    if (A->rel) return GRB_SUCCESS;
+    if (A->rel || A->rel_checked) return GRB_SUCCESS;
     if (A->nrows != A->ncols || A->vals.p || A->nrows <= 0) return GRB_INVALID_VALUE;
     const int64_t n = A->nrows;
-    Matrix* R = new Matrix();
-    R->ctx = c;
-    R->type = A->type;
-    R->nrows = A->nrows;
-    R->ncols = A->ncols;
-    R->nnz = A->nnz;
-    R->iso_val = A->iso_val;
-    R->nonempty_rows = A->nonempty_rows;
-    R->row_ptr = buf_alloc(c, sizeof(int32_t) * (size_t)(n + 1));
-    R->col_idx = buf_alloc(c, sizeof(int32_t) * (size_t)padded_nnz(A->nnz));
+    auto af = [](void* x, size_t b) { return dev_alloc((Ctx*)x, b); };
+    auto ff = [](void* x, void* q, size_t b) { dev_free((Ctx*)x, q, b); };
     DevBuf n2o = buf_alloc(c, sizeof(int32_t) * (size_t)n), o2n = buf_alloc(c, sizeof(int32_t) * (size_t)n);
-    grb_info st = (R->row_ptr.p && R->col_idx.p && n2o.p && o2n.p) ? GRB_SUCCESS : GRB_OUT_OF_MEMORY;
+    grb_info st = (n2o.p && o2n.p) ? GRB_SUCCESS : GRB_OUT_OF_MEMORY;
+    RelabelArgs a;
+    a.n = (int32_t)n;
+    a.nnz = A->nnz;
+    a.row_ptr = (const int32_t*)A->row_ptr.p;
+    a.col_idx = (const int32_t*)A->col_idx.p;
+    a.new_row_ptr = nullptr;
+    a.new_col_idx = nullptr;
+    a.new2old = (int32_t*)n2o.p;
+    a.old2new = (int32_t*)o2n.p;
+    a.top_h = REL_TOP;
+    unsigned long long top = 0;
     if (!st) {
-        RelabelArgs a;
-        a.n = (int32_t)n;
-        a.nnz = A->nnz;
-        a.row_ptr = (const int32_t*)A->row_ptr.p;
-        a.col_idx = (const int32_t*)A->col_idx.p;
+        st = cuda_check(c, relabel_order(c->stream, a, &top, af, ff, c), "relabel order");
+        c->stats.kernel_launches += 6;
+    }
+    if (!st && (double)top < REL_MIN_COVER * (double)A->nnz) {
+        A->rel_checked = true;
+        buf_free(c, n2o);
+        buf_free(c, o2n);
+        return GRB_SUCCESS;
+    }
+    Matrix* R = nullptr;
+    if (!st) {
+        R = new Matrix();
+        R->ctx = c;
+        R->type = A->type;
+        R->nrows = A->nrows;
+        R->ncols = A->ncols;
+        R->nnz = A->nnz;
+        R->iso_val = A->iso_val;
+        R->nonempty_rows = A->nonempty_rows;
+        R->row_ptr = buf_alloc(c, sizeof(int32_t) * (size_t)(n + 1));
+        R->col_idx = buf_alloc(c, sizeof(int32_t) * (size_t)padded_nnz(A->nnz));
+        if (!R->row_ptr.p || !R->col_idx.p) st = GRB_OUT_OF_MEMORY;
+    }
+    if (!st) {
         a.new_row_ptr = (int32_t*)R->row_ptr.p;
         a.new_col_idx = (int32_t*)R->col_idx.p;
-        a.new2old = (int32_t*)n2o.p;
-        a.old2new = (int32_t*)o2n.p;
-        st = cuda_check(c, relabel_csr(c->stream, a, [](void* x, size_t b) { return dev_alloc((Ctx*)x, b); },
-                                       [](void* x, void* q, size_t b) { dev_free((Ctx*)x, q, b); }, c),
-                        "relabel");
-        c->stats.kernel_launches += 9;
+        st = cuda_check(c, relabel_build(c->stream, a, af, ff, c), "relabel build");
+        c->stats.kernel_launches += 4;
     }
     if (st) {
-        matrix_unref(R);
+        if (R) matrix_unref(R);
         buf_free(c, n2o);
         buf_free(c, o2n);
         return st;
     }
     A->rel = R;
+    A->rel_checked = true;
     A->new2old = n2o;
     A->old2new = o2n;
     A->rel_id = c->next_id++;

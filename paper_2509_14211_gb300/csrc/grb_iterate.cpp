@@ -234,13 +234,13 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     const int64_t n = A->nrows;
     // AL: the matrix the loop kernels run on (A, or its degree-ordered copy;
     // then every vector the kernels read or write is in that vertex order)
-    const bool rel = c->relabel;
     grb_info st = GRB_SUCCESS;
     Matrix* AL = A;
-    if (rel) {
+    if (c->relabel) {
         st = ensure_relabel(c, A);
-        if (!st) AL = A->rel;
+        if (!st && A->rel) AL = A->rel;
     }
+    const bool rel = AL != A;
     if (!st) st = ensure_plan(c, AL);
     if (!st && lm.uniform) st = ensure_sinkbits(c, lm.sinks);
     if (!st && rel) st = ensure_perm_copy(c, A, lm.d, false);

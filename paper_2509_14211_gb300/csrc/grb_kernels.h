@@ -224,13 +224,16 @@ cudaError_t build_row_plan(cudaStream_t st, const PlanArgs& a, AllocFn af, FreeF
 
 // Vertex relabelling by descending degree (stable): new2old[k] = vertex
 // with the k-th largest degree, old2new its inverse (synchronises).
+// *top_sum (host, optional) = sum of the top_h largest degrees.
 cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t* new2old, int32_t* old2new,
-                         AllocFn af, FreeFn ff, void* actx);
+                         AllocFn af, FreeFn ff, void* actx, int32_t top_h = 0, unsigned long long* top_sum = nullptr);
 // Symmetric relabelling of a square pattern CSR matrix (A^T) by descending
 // column count (the out-degree of the graph): new row k = old row new2old[k]
 // with every column j renamed old2new[j], entries kept in their old order.
-// Outputs are preallocated: new_row_ptr[n+1], new_col_idx[padded_nnz(nnz)],
-// new2old[n], old2new[n].  Synchronises.
+// relabel_order computes new2old / old2new and *top_sum (host) = the number
+// of nonzeros in the top_h columns of largest count; relabel_build then
+// writes new_row_ptr[n+1] and new_col_idx[padded_nnz(nnz)].  Both
+// synchronise; outputs are preallocated by the caller.
 struct RelabelArgs {
     int32_t n;
     int64_t nnz;
@@ -240,8 +243,11 @@ struct RelabelArgs {
     int32_t* new_col_idx;
     int32_t* new2old;
     int32_t* old2new;
+    int32_t top_h;
 };
-cudaError_t relabel_csr(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx);
+cudaError_t relabel_order(cudaStream_t st, const RelabelArgs& a, unsigned long long* top_sum, AllocFn af, FreeFn ff,
+                          void* actx);
+cudaError_t relabel_build(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx);
 // out[k] = in[perm[k]] for 4- or 8-byte elements.
 cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, const void* in, void* out, int32_t esize);
 // bit k of out = bit new2old[k] of in.

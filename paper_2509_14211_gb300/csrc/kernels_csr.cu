@@ -387,8 +387,15 @@ cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* 
     return cudaGetLastError();
 }
 
+__global__ void sum_prefix_kernel(int32_t h, const int32_t* __restrict__ v, unsigned long long* out) {
+    unsigned long long c = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < h; i += gridDim.x * blockDim.x) c += (unsigned)v[i];
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t* new2old, int32_t* old2new,
-                         AllocFn af, FreeFn ff, void* actx) {
+                         AllocFn af, FreeFn ff, void* actx, int32_t top_h, unsigned long long* top_sum) {
     Scratch S{af, ff, actx, {}};
     cudaError_t e;
     int32_t* ids = (int32_t*)S.get(sizeof(int32_t) * n);
@@ -408,10 +415,22 @@ cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t
         return e;
     invert_perm_kernel<<<grid_for(n), 256, 0, st>>>(n, new2old, old2new);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (top_sum) {
+        // edges whose source is among the top_h vertices (keys_out is sorted)
+        unsigned long long* d = (unsigned long long*)S.get(sizeof(unsigned long long));
+        if (!d) return cudaErrorMemoryAllocation;
+        if ((e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        const int32_t h = top_h < n ? top_h : n;
+        if (h > 0) sum_prefix_kernel<<<grid_for(h), 256, 0, st>>>(h, keys_out, d);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(top_sum, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return e;
+    }
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t relabel_csr(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx) {
+cudaError_t relabel_order(cudaStream_t st, const RelabelArgs& a, unsigned long long* top_sum, AllocFn af, FreeFn ff,
+                          void* actx) {
     Scratch S{af, ff, actx, {}};
     cudaError_t e;
     const int32_t n = a.n;
@@ -420,7 +439,15 @@ cudaError_t relabel_csr(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeF
     if ((e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st)) != cudaSuccess) return e;
     if (a.nnz > 0) col_count_kernel<<<grid_for(a.nnz), 256, 0, st>>>(a.nnz, a.col_idx, deg);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = degree_order(st, n, deg, a.new2old, a.old2new, af, ff, actx)) != cudaSuccess) return e;
+    return degree_order(st, n, deg, a.new2old, a.old2new, af, ff, actx, a.top_h, top_sum);
+}
+
+cudaError_t relabel_build(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx) {
+    Scratch S{af, ff, actx, {}};
+    cudaError_t e;
+    const int32_t n = a.n;
+    int32_t* deg = (int32_t*)S.get(sizeof(int32_t) * (n + 1));
+    if (!deg) return cudaErrorMemoryAllocation;
     relabel_rowlen_kernel<<<grid_for(n + 1), 256, 0, st>>>(n, a.row_ptr, a.new2old, deg);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     size_t tb = 0;

@@ -582,6 +582,7 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
     reduce_parts<T, BLK>(p.part, G_, R, D, sm);
     T tele = p.tele_from_slot ? (T)round_to(p.out.type, schain_apply(p.chain, D)) : (T)p.tele_const;
     double rd = p.rdiff0;
+    double rd_prev = rd;
     int it = 0;
     while (it < p.iters && rd > p.tol) {
         TileIO<T, G> io{};
@@ -621,9 +622,15 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
         if (p.tele_from_slot) tele = (T)round_to(p.out.type, schain_apply(p.chain, D));
         if (blockIdx.x == 0 && threadIdx.x == 0 && p.hist) p.hist[it] = rd;
         ++it;
-        // mixed precision: once the residual is small, rebuild w in FP32 from
-        // the rank just written and gather FP32 from the next body on
-        if (p.mixed && !phase32 && rd < p.mixed_switch && it < p.iters && rd > p.tol) {
+        // mixed precision: once the residual is small -- or has stopped
+        // falling, i.e. the BF16 rounding floor is reached (one body whose
+        // residual fell by less than 5%; in exact arithmetic the L1 change
+        // contracts at least by the damping factor each body) -- rebuild w in
+        // FP32 from the rank just written and gather FP32 from the next body
+        // on.  Every CTA sees the same residuals, so all take the same decision.
+        const bool stalled = it > 1 && rd > 0.95 * rd_prev;
+        rd_prev = rd;
+        if (p.mixed && !phase32 && (rd < p.mixed_switch || stalled) && it < p.iters && rd > p.tol) {
             const T* rcur = reinterpret_cast<const T*>(p.rbuf[(it - 1) & 1]);
             float* w32 = reinterpret_cast<float*>(p.wbuf32[it & 1]);
             for (int i = blockIdx.x * BLK + threadIdx.x; i < p.nrows; i += G_ * BLK)

@@ -115,6 +115,39 @@ def test_fp32_full_size_rmat22(grb):
     assert abs(np.sum(r) - 1.0) < 1e-4 and np.all(r >= 0)
 
 
+# Mixed precision stops at an L1 change of 1e-6 (1-d)/d: by the L1
+# contraction of the PageRank map, ||r - r*||_1 <= d/(1-d) * change <= 1e-6.
+MIXED_TOL = 1e-6 * (1 - D) / D
+
+
+def test_mixed_precision_er20_matches_converged_oracle(grb):
+    """Erdos-Renyi, 2^20 vertices, out-degree 16, 2% sinks: BF16 gathers until
+    the residual falls below 1e-3 (or stalls), then FP32; the result must be
+    within L1 1e-6 of the FP64 oracle converged to 1e-13."""
+    n = 1 << 20
+    src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
+    r, it, _, (hist, phase) = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", MIXED_TOL, 500,
+                                   persistent=1, mixed=True)
+    assert phase == 1 and it < 500 and hist[-1] <= MIXED_TOL
+    ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=1e-13, itermax=1000, mode="uniform")
+    assert np.sum(np.abs(r - ref)) <= 1e-6
+
+
+@pytest.mark.slow
+def test_mixed_precision_er24_full_size_properties(grb):
+    """The full mixed-precision configuration (2^24 vertices, ~268M edges):
+    properties that hold at any size -- the switch happened, the stop rule was
+    met, ranks are non-negative and sum to 1 (uniform dangling), and the
+    residual falls after the switch."""
+    n = 1 << 24
+    src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
+    r, it, _, (hist, phase) = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", MIXED_TOL, 500,
+                                   persistent=1, mixed=True)
+    assert phase == 1 and it < 500 and hist[-1] <= MIXED_TOL
+    assert np.all(r >= 0) and abs(np.sum(r.astype(np.float64)) - 1.0) < 1e-4
+    assert np.all(np.diff(hist[-10:]) < 0)
+
+
 def test_mixed_precision_refines_to_fp32(grb):
     n = 1 << 15
     src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
