@@ -631,10 +631,41 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
         const bool stalled = it > 1 && rd > 0.95 * rd_prev;
         rd_prev = rd;
         if (p.mixed && !phase32 && (rd < p.mixed_switch || stalled) && it < p.iters && rd > p.tol) {
-            const T* rcur = reinterpret_cast<const T*>(p.rbuf[(it - 1) & 1]);
+            T* rcur = reinterpret_cast<T*>(p.rbuf[(it - 1) & 1]);
             float* w32 = reinterpret_cast<float*>(p.wbuf32[it & 1]);
-            for (int i = blockIdx.x * BLK + threadIdx.x; i < p.nrows; i += G_ * BLK)
-                w32[i] = (float)(__ldcg(rcur + i) / dd[i]);
+            // With uniform dangling the rank sum is invariant (1) in exact
+            // arithmetic, but BF16 rounding of nearly equal ranks is
+            // correlated and shifts it; a mass error only decays by the
+            // damping factor per body, so the FP32 phase would crawl.  The
+            // rank is renormalised to unit sum once, at the switch (the fixed
+            // point is unchanged).  Each CTA scales only its own entries.
+            double scale = 1.0;
+            if (p.tele_from_slot) {
+                double ms = 0.0;
+                for (int i = blockIdx.x * BLK + threadIdx.x; i < p.nrows; i += G_ * BLK) ms += (double)__ldcg(rcur + i);
+                ms = block_sum_d<BLK>(ms, sm.red);
+                // the partial buffer the body just read stays untouched; the
+                // other one is next written after two more grid barriers
+                double* part2 = p.part + 2 * G_ * ((it + 1) & 1);
+                if (threadIdx.x == 0) {
+                    part2[2 * blockIdx.x] = ms;
+                    part2[2 * blockIdx.x + 1] = 0.0;
+                }
+                if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
+                double M, Z;
+                reduce_parts<T, BLK>(part2, G_, M, Z, sm);
+                if (M > 0.0) scale = 1.0 / M;
+                D *= scale;
+                tele = (T)round_to(p.out.type, schain_apply(p.chain, D));
+            }
+            for (int i = blockIdx.x * BLK + threadIdx.x; i < p.nrows; i += G_ * BLK) {
+                T rv = __ldcg(rcur + i);
+                if (scale != 1.0) {
+                    rv = (T)((double)rv * scale);
+                    rcur[i] = rv;
+                }
+                w32[i] = (float)(rv / dd[i]);
+            }
             phase32 = 1;
             if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
         }
