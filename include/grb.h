@@ -293,6 +293,60 @@ grb_info grb_iterate_end(grb_context ctx, grb_scalar cond, double tol, int64_t i
  * switched to the FP32 gather, 0 when it did not, -1 for other loops. */
 grb_info grb_iterate_history(grb_context ctx, double* hist, int64_t cap, int64_t* n, int32_t* mixed_phase);
 
+/* ------------------------------- batched personalised PageRank (extension)
+ *
+ * The paper computes one PageRank vector (§IV).  A grb_ppr runs that same
+ * fused iteration for up to GRB_PPR_MAX_SLOTS personalisation vectors
+ * ("slots") over one matrix at once, as one sparse x dense product per body:
+ * for slot s with seed set S (duplicates collapsed),
+ *     v = 1/|S| on S,  r_0 = v,
+ *     r' = (1 - damping) v + damping D / n + A^T (r ./ d),
+ *     d = max(out-degree, 1) / damping,  D = sum of r over vertices
+ *     without out-edges (dangling mass spread uniformly),
+ *     rdiff = sum |r - r'|  (FP64),
+ * and the §IV loop test `while iter <= itermax && rdiff > tol` applied to
+ * each slot separately after every body; a slot whose test fails keeps its
+ * rank while the others go on.  Ranks are FP32.  A slot's results do not
+ * depend on the other slots or on its position (fixed summation orders).
+ * Slots may be set, cleared and refilled between runs, which is how a serving
+ * loop admits queries while others are in flight.
+ *
+ * The matrix is A^T as built by grb_matrix_build_csr(TRANSPOSE): row i lists
+ * the sources of the edges into i; it must be square and pattern-only; the
+ * grb_ppr holds a reference to it.  Release a grb_ppr with grb_free. */
+typedef struct grb_ppr_s* grb_ppr;
+#define GRB_PPR_MAX_SLOTS 128
+
+/* New batch object with `slots` slots (rounded up to a multiple of 32;
+ * grb_ppr_slots returns the count), all empty.  Device memory: about
+ * 16 * n * slots bytes.  Errors: GRB_NULL_POINTER, GRB_UNINITIALIZED_OBJECT,
+ * GRB_INVALID_VALUE (non-square or valued matrix, slots outside
+ * 1..GRB_PPR_MAX_SLOTS, damping outside [0, 1)), GRB_OUT_OF_MEMORY. */
+grb_info grb_ppr_new(grb_ppr* P, grb_matrix AT, double damping, int32_t slots);
+grb_info grb_ppr_slots(grb_ppr P, int32_t* slots);
+
+/* Start a query in `slot` (replacing whatever it held): seeds are host
+ * vertex ids (nseeds >= 1; copied), tol and itermax its loop test.
+ * Errors: GRB_INVALID_VALUE (slot, nseeds or itermax out of range),
+ * GRB_INVALID_INDEX (a seed outside [0, n)). */
+grb_info grb_ppr_set(grb_ppr P, int32_t slot, const int32_t* seeds, int64_t nseeds, double tol, int64_t itermax);
+
+/* Stop and empty a slot. */
+grb_info grb_ppr_clear(grb_ppr P, int32_t slot);
+
+/* Enqueue `iters` bodies (0..100000) for every active slot on the context's
+ * stream (captured once per iteration count as a CUDA graph) and return. */
+grb_info grb_ppr_run(grb_ppr P, int64_t iters);
+
+/* Per slot (host arrays of grb_ppr_slots entries, each optional): 1 while
+ * the slot's loop goes on, the bodies it has run, its last rdiff (1 before
+ * the first body).  Waits for the queued work. */
+grb_info grb_ppr_status(grb_ppr P, int32_t* active, int64_t* iters, double* resid);
+
+/* The current rank vector of a slot: n FP32 values into `ranks` (host
+ * memory, or device memory when out_is_device).  Waits for the queued work. */
+grb_info grb_ppr_get(grb_ppr P, int32_t slot, float* ranks, int out_is_device);
+
 /* ------------------------------------------------ allocation-free call */
 
 /* The paper has no counterpart to this call; it serves callers that cannot

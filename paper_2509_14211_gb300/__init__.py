@@ -119,6 +119,13 @@ def _declare(lib):
         "grb_error": [V],
         "grb_selftest_wait_timeout": [V, I64],
         "grb_reduce_dense_noalloc": [V, I, U64, I, V, V],
+        "grb_ppr_new": [P(V), V, D, ctypes.c_int32],
+        "grb_ppr_slots": [V, P(ctypes.c_int32)],
+        "grb_ppr_set": [V, ctypes.c_int32, V, I64, D, I64],
+        "grb_ppr_clear": [V, ctypes.c_int32],
+        "grb_ppr_run": [V, I64],
+        "grb_ppr_status": [V, V, V, V],
+        "grb_ppr_get": [V, ctypes.c_int32, V, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -151,7 +158,9 @@ def symbols():
                         "grb_apply", "grb_apply_bind2nd", "grb_apply_bind2nd_scalar", "grb_assign_scalar",
                         "grb_mxv", "grb_ewise_add", "grb_ewise_mult", "grb_reduce", "grb_wait",
                         "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
-                        "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc") if hasattr(lib, n)]
+                        "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc", "grb_ppr_new", "grb_ppr_slots",
+                        "grb_ppr_set", "grb_ppr_clear", "grb_ppr_run", "grb_ppr_status", "grb_ppr_get")
+            if hasattr(lib, n)]
 
 
 def _check(rc: int, where: str, obj=None) -> int:
@@ -398,6 +407,56 @@ def grb_iterate_history(ctx):
     _check(load().grb_iterate_history(ctx, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
                                       ctypes.byref(n), ctypes.byref(ph)), "grb_iterate_history", ctx)
     return h[:n.value], ph.value
+
+
+# ------------------------------------------- batched personalised PageRank
+GRB_PPR_MAX_SLOTS = 128
+
+
+def grb_ppr_new(AT: int, damping: float, slots: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().grb_ppr_new(ctypes.byref(out), AT, float(damping), int(slots)), "grb_ppr_new", AT)
+    return out.value
+
+
+def grb_ppr_slots(P: int) -> int:
+    k = ctypes.c_int32()
+    _check(load().grb_ppr_slots(P, ctypes.byref(k)), "grb_ppr_slots")
+    return k.value
+
+
+def grb_ppr_set(P: int, slot: int, seeds, tol: float, itermax: int) -> None:
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    _check(load().grb_ppr_set(P, int(slot), seeds.ctypes.data, len(seeds), float(tol), int(itermax)), "grb_ppr_set")
+
+
+def grb_ppr_clear(P: int, slot: int) -> None:
+    _check(load().grb_ppr_clear(P, int(slot)), "grb_ppr_clear")
+
+
+def grb_ppr_run(P: int, iters: int) -> None:
+    _check(load().grb_ppr_run(P, int(iters)), "grb_ppr_run")
+
+
+def grb_ppr_status(P: int):
+    """(active[slots] int32, iters[slots] int64, resid[slots] float64)."""
+    k = grb_ppr_slots(P)
+    a = np.empty(k, np.int32)
+    it = np.empty(k, np.int64)
+    rs = np.empty(k, np.float64)
+    _check(load().grb_ppr_status(P, a.ctypes.data, it.ctypes.data, rs.ctypes.data), "grb_ppr_status")
+    return a, it, rs
+
+
+def grb_ppr_get(P: int, slot: int, n: int, out=None):
+    """Slot's ranks: into a new host float32 array, or into `out` (a device
+    tensor of n float32)."""
+    if out is not None:
+        _check(load().grb_ppr_get(P, int(slot), _ptr(out), 1), "grb_ppr_get")
+        return out
+    r = np.empty(n, np.float32)
+    _check(load().grb_ppr_get(P, int(slot), r.ctypes.data, 0), "grb_ppr_get")
+    return r
 
 
 def grb_free(obj) -> None:

@@ -881,6 +881,8 @@ grb_info grb_free(void** obj) {
         Matrix* A = reinterpret_cast<Matrix*>(*obj);
         A->handle_alive = false;
         matrix_unref(A);
+    } else if (k == Kind::PPR) {
+        ppr_destroy(reinterpret_cast<Ppr*>(*obj));
     } else if (k == Kind::CONTEXT) {
         Ctx* c = reinterpret_cast<Ctx*>(*obj);
         cudaStreamSynchronize(c->stream);

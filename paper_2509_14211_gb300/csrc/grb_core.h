@@ -23,7 +23,7 @@
 
 namespace grb {
 
-enum class Kind : uint32_t { CONTEXT = 0x47524230u, MATRIX, VECTOR, SCALAR, DEAD = 0xDEADDEADu };
+enum class Kind : uint32_t { CONTEXT = 0x47524230u, MATRIX, VECTOR, SCALAR, PPR, DEAD = 0xDEADDEADu };
 
 struct Ctx;
 struct Node;
@@ -229,6 +229,8 @@ grb_info ensure_plan(Ctx* c, Matrix* A);
 grb_info ensure_sinkbits(Ctx* c, Version* sinks);
 grb_info ensure_relabel(Ctx* c, Matrix* A);
 grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits);
+struct Ppr;
+void ppr_destroy(Ppr* P);
 grb_info read_status(Ctx* c);
 PrParams plan_params_of(Ctx* c, Matrix* A);
 int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n = 0);

@@ -7,6 +7,8 @@
 
 #include <cstdint>
 
+#include "grb.h"
+
 namespace grb {
 
 enum class Fmt : int32_t { EMPTY = 0, ISO = 1, FULL = 2, BITMAP = 3 };
@@ -253,6 +255,88 @@ cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, cons
 // bit k of out = bit new2old[k] of in.
 cudaError_t launch_permute_bits(cudaStream_t st, int32_t n, const int32_t* new2old, const uint32_t* in_bits,
                                 uint32_t* out_bits);
+// ------------------------------------------------ batched personalised PageRank
+// k queries ("slots") iterate together over one A^T: ranks are stored as
+// [k-tile][n][PPR_LANES] FP32, so one slot is one lane of a warp and the
+// gather of a source vertex's values for a k-tile is one 128-byte line.
+constexpr int PPR_LANES = 32;
+constexpr int PPR_BLOCK = 512;
+constexpr int PPR_MAX_SLOTS = GRB_PPR_MAX_SLOTS;   // 4 k-tiles
+
+struct PprParams {
+    // A^T and its row-gather plan
+    const int32_t* col_idx = nullptr;
+    int32_t nrows = 0, nnz = 0, ntiles = 0;
+    const uint32_t* tile_meta = nullptr;
+    const uint32_t* rowend_bits = nullptr;
+    const int32_t* ne_rows = nullptr;
+    int32_t n_ne = 0;
+    const int32_t* empty_rows = nullptr;
+    int32_t n_empty = 0;
+    const FixDesc* fix = nullptr;
+    // ranks and gather values, [kt][n][32]
+    int32_t kt = 0;
+    const float* r_old = nullptr;
+    float* r_new = nullptr;
+    const float* w_old = nullptr;
+    float* w_new = nullptr;
+    const float* dd = nullptr;          // n: max(outdeg, 1) / damping
+    const uint32_t* sinkbits = nullptr; // n bits: no out-edges
+    float* agg = nullptr;               // [kt][ntiles][32] carry of the row open at a tile's end
+    float* first = nullptr;             // [kt][ntiles][32] a tile's part of its split first row
+    // teleport (1 - damping) v_s: seeds sorted by (k-tile, row, lane)
+    const uint32_t* seedbits = nullptr; // n bits: a seed of some slot
+    const int32_t* seed_ptr = nullptr;  // kt + 1 offsets
+    const int32_t* seed_row = nullptr;
+    const int32_t* seed_lane = nullptr;
+    const float* seed_val = nullptr;
+    // slot state
+    const int32_t* active = nullptr;    // kt*32
+    const float* tele_base = nullptr;   // kt*32: damping * D_s / n
+    double* part = nullptr;             // [grid][kt*32][2] residual, dangling mass
+};
+
+struct PprFinish {
+    int32_t slots = 0, grid_a = 0, grid_b = 0;
+    const double* part_a = nullptr;
+    const double* part_b = nullptr;
+    int32_t* active = nullptr;
+    int32_t* iters = nullptr;
+    const int32_t* itermax = nullptr;
+    const double* tol = nullptr;
+    double* resid = nullptr;
+    float* tele_base = nullptr;
+    double damping = 0.85;
+    int64_t n = 0;
+};
+
+struct PprInit {
+    int32_t slot = 0, nseeds = 0, nrows = 0;
+    const int32_t* seeds = nullptr;     // device, deduplicated
+    float r0 = 0.f;                     // 1 / nseeds
+    float* r = nullptr;                 // current rank buffer [kt][n][32]
+    float* w = nullptr;
+    const float* dd = nullptr;
+    const uint32_t* sinkbits = nullptr;
+    float* tele_base = nullptr;
+    double damping = 0.85;
+};
+
+cudaError_t launch_ppr_tiles(cudaStream_t st, const PprParams& p, int grid);
+cudaError_t launch_ppr_fixups(cudaStream_t st, const PprParams& p, int grid);
+cudaError_t launch_ppr_finish(cudaStream_t st, const PprFinish& f);
+// Zero a slot's column of r and w, then place its start vector (1/nseeds at
+// each seed) and its first dangling-mass term.
+cudaError_t launch_ppr_init_slot(cudaStream_t st, const PprInit& a);
+// Bits of every seed vertex (bits cleared first; nbits words of 32).
+cudaError_t launch_ppr_seedbits(cudaStream_t st, int32_t nseeds, const int32_t* rows, uint32_t* bits, int64_t nwords);
+// out[i] = r[kt][i][lane] of one slot.
+cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32_t slot, float* out);
+// FP32 divisor max(deg/damping, 1/damping) and sink bits from column counts.
+cudaError_t launch_ppr_divisor(cudaStream_t st, int32_t n, const int32_t* deg, double damping, float* dd,
+                               uint32_t* sinkbits);
+int ppr_blocks_per_sm();
+
 // Resident CTAs per SM of the fused kernel for the given rank / gather types
 // (hot_n > 0: the persistent kernel with a hot copy of hot_n entries; 0 when
 // that configuration cannot run).

@@ -1,0 +1,410 @@
+// Batched personalised PageRank (grb_ppr_*): k query slots over one A^T,
+// iterated together by kernels_ppr.cu.  The paper runs one rank vector per
+// PageRank; the slots here are that same fused iteration for many
+// personalisation vectors at once, the form a serving loop needs: a slot
+// can be (re)filled between runs while the others keep their state.
+//
+// Per slot: seeds S (deduplicated), teleport v = uniform over S, start
+// vector r_0 = v, dangling mass spread uniformly, loop test of the §IV
+// listing (`while iter <= itermax && rdiff > tol`) evaluated on the device
+// after every body; a slot whose test fails keeps its rank.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "grb_core.h"
+
+namespace grb {
+
+struct Ppr {
+    Kind kind = Kind::PPR;
+    Ctx* c = nullptr;
+    Matrix* A = nullptr;
+    double damping = 0.85;
+    int32_t slots = 0, kt = 0;
+    int64_t n = 0;
+    int grid = 0;
+    int cur = 0;                       // which of r[2] / w[2] holds the current iterate
+    DevBuf r[2], w[2], dd, sinkbits, seedbits, agg, first, part_a, part_b;
+    DevBuf active, iters, itermax, tol, resid, tele;
+    DevBuf seed_ptr, seed_row, seed_lane, seed_val;
+    std::vector<std::vector<int32_t>> seeds;
+    bool dirty = true;
+    cudaGraphExec_t exec = nullptr;
+    int64_t exec_iters = 0;
+    int exec_cur = -1;
+};
+
+namespace {
+
+Ppr* as_ppr(grb_ppr p) {
+    Ppr* x = reinterpret_cast<Ppr*>(p);
+    return (x && x->kind == Kind::PPR) ? x : nullptr;
+}
+
+void drop_graph(Ppr* P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+    P->exec_cur = -1;
+}
+
+// Seed arrays sorted by (k-tile, row, lane) and the seed bitmap.
+grb_info upload_seeds(Ppr* P) {
+    Ctx* c = P->c;
+    struct E { int32_t kt, row, lane; float val; };
+    std::vector<E> es;
+    for (int32_t s = 0; s < P->slots; ++s) {
+        const auto& S = P->seeds[s];
+        if (S.empty()) continue;
+        const float val = (float)((1.0 - P->damping) * (1.0 / (double)S.size()));
+        for (int32_t v : S) es.push_back({s / PPR_LANES, v, s % PPR_LANES, val});
+    }
+    std::sort(es.begin(), es.end(), [](const E& a, const E& b) {
+        return a.kt != b.kt ? a.kt < b.kt : a.row != b.row ? a.row < b.row : a.lane < b.lane;
+    });
+    const size_t ne = es.size();
+    std::vector<int32_t> ptr(P->kt + 1, 0), row(ne ? ne : 1), lane(ne ? ne : 1);
+    std::vector<float> val(ne ? ne : 1);
+    for (size_t q = 0; q < ne; ++q) {
+        ptr[es[q].kt + 1]++;
+        row[q] = es[q].row;
+        lane[q] = es[q].lane;
+        val[q] = es[q].val;
+    }
+    for (int32_t k = 0; k < P->kt; ++k) ptr[k + 1] += ptr[k];
+    drop_graph(P);
+    for (DevBuf* b : {&P->seed_ptr, &P->seed_row, &P->seed_lane, &P->seed_val}) buf_free(c, *b);
+    P->seed_ptr = buf_alloc(c, sizeof(int32_t) * ptr.size());
+    P->seed_row = buf_alloc(c, sizeof(int32_t) * row.size());
+    P->seed_lane = buf_alloc(c, sizeof(int32_t) * lane.size());
+    P->seed_val = buf_alloc(c, sizeof(float) * val.size());
+    if (!P->seed_ptr.p || !P->seed_row.p || !P->seed_lane.p || !P->seed_val.p) return GRB_OUT_OF_MEMORY;
+    grb_info st = cuda_check(c, cudaMemcpyAsync(P->seed_ptr.p, ptr.data(), sizeof(int32_t) * ptr.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "seed upload");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(P->seed_row.p, row.data(), sizeof(int32_t) * row.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "seed upload");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(P->seed_lane.p, lane.data(), sizeof(int32_t) * lane.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "seed upload");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(P->seed_val.p, val.data(), sizeof(float) * val.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "seed upload");
+    if (!st) {
+        c->stats.kernel_launches++;
+        st = cuda_check(c, launch_ppr_seedbits(c->stream, (int32_t)ne, (const int32_t*)P->seed_row.p,
+                                               (uint32_t*)P->seedbits.p, (P->n + 31) / 32), "seed bits");
+    }
+    // the host vectors above must outlive the copies
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "seed upload");
+    if (!st) P->dirty = false;
+    return st;
+}
+
+PprParams params(Ppr* P, int from) {
+    TilePlan* pl = P->A->plan;
+    PprParams p;
+    p.col_idx = (const int32_t*)P->A->col_idx.p;
+    p.nrows = (int32_t)P->n;
+    p.nnz = (int32_t)P->A->nnz;
+    p.ntiles = (int32_t)pl->ntiles;
+    p.tile_meta = (const uint32_t*)pl->meta.p;
+    p.rowend_bits = (const uint32_t*)pl->rowend_bits.p;
+    p.ne_rows = (const int32_t*)pl->ne_rows.p;
+    p.n_ne = (int32_t)pl->n_ne;
+    p.empty_rows = (const int32_t*)pl->empty_rows.p;
+    p.n_empty = (int32_t)pl->n_empty;
+    p.fix = (const FixDesc*)pl->fix.p;
+    p.kt = P->kt;
+    p.r_old = (const float*)P->r[from].p;
+    p.r_new = (float*)P->r[from ^ 1].p;
+    p.w_old = (const float*)P->w[from].p;
+    p.w_new = (float*)P->w[from ^ 1].p;
+    p.dd = (const float*)P->dd.p;
+    p.sinkbits = (const uint32_t*)P->sinkbits.p;
+    p.agg = (float*)P->agg.p;
+    p.first = (float*)P->first.p;
+    p.seedbits = (const uint32_t*)P->seedbits.p;
+    p.seed_ptr = (const int32_t*)P->seed_ptr.p;
+    p.seed_row = (const int32_t*)P->seed_row.p;
+    p.seed_lane = (const int32_t*)P->seed_lane.p;
+    p.seed_val = (const float*)P->seed_val.p;
+    p.active = (const int32_t*)P->active.p;
+    p.tele_base = (const float*)P->tele.p;
+    return p;
+}
+
+grb_info record_iterations(Ppr* P, cudaStream_t st, int64_t iters) {
+    const int S = P->kt * PPR_LANES;
+    PprFinish f;
+    f.slots = S;
+    f.grid_a = P->grid;
+    f.grid_b = P->grid;
+    f.part_a = (const double*)P->part_a.p;
+    f.part_b = (const double*)P->part_b.p;
+    f.active = (int32_t*)P->active.p;
+    f.iters = (int32_t*)P->iters.p;
+    f.itermax = (const int32_t*)P->itermax.p;
+    f.tol = (const double*)P->tol.p;
+    f.resid = (double*)P->resid.p;
+    f.tele_base = (float*)P->tele.p;
+    f.damping = P->damping;
+    f.n = P->n;
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < iters && e == cudaSuccess; ++k) {
+        PprParams p = params(P, (int)((P->cur + k) & 1));
+        p.part = (double*)P->part_a.p;
+        e = launch_ppr_tiles(st, p, P->grid);
+        if (e == cudaSuccess) {
+            p.part = (double*)P->part_b.p;
+            e = launch_ppr_fixups(st, p, P->grid);
+        }
+        if (e == cudaSuccess) e = launch_ppr_finish(st, f);
+    }
+    return cuda_check(P->c, e, "ppr iteration");
+}
+
+}  // namespace
+
+void ppr_destroy(Ppr* P) {
+    Ctx* c = P->c;
+    cudaStreamSynchronize(c->stream);
+    drop_graph(P);
+    for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->dd, &P->sinkbits, &P->seedbits, &P->agg,
+                      &P->first, &P->part_a, &P->part_b, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid,
+                      &P->tele, &P->seed_ptr, &P->seed_row, &P->seed_lane, &P->seed_val})
+        buf_free(c, *b);
+    matrix_unref(P->A);
+    P->kind = Kind::DEAD;
+    delete P;
+}
+
+}  // namespace grb
+
+using namespace grb;
+
+extern "C" {
+
+grb_info grb_ppr_new(grb_ppr* out, grb_matrix Am, double damping, int32_t slots) {
+    if (!out || !Am) return GRB_NULL_POINTER;
+    *out = nullptr;
+    Matrix* A = reinterpret_cast<Matrix*>(Am);
+    if (A->kind != Kind::MATRIX) return GRB_UNINITIALIZED_OBJECT;
+    if (A->nrows != A->ncols || A->vals.p) return GRB_INVALID_VALUE;      // square pattern A^T
+    if (A->nrows < 1 || A->nrows + A->nnz >= ((int64_t)1 << 31)) return GRB_INVALID_VALUE;
+    if (slots < 1 || slots > PPR_MAX_SLOTS || !(damping >= 0.0 && damping < 1.0)) return GRB_INVALID_VALUE;
+    Ctx* c = A->ctx;
+    grb_info st = ensure_plan(c, A);
+    if (st) return st;
+    Ppr* P = new Ppr();
+    P->c = c;
+    P->A = A;
+    A->refs++;
+    P->damping = damping;
+    P->kt = (slots + PPR_LANES - 1) / PPR_LANES;
+    P->slots = P->kt * PPR_LANES;
+    P->n = A->nrows;
+    P->seeds.assign(P->slots, {});
+    P->grid = ppr_blocks_per_sm() * c->sm_count;
+    const int64_t n = P->n, S = P->slots, nt = A->plan->ntiles;
+    const size_t rb = sizeof(float) * (size_t)P->kt * (size_t)n * PPR_LANES;
+    for (int q = 0; q < 2; ++q) {
+        P->r[q] = buf_alloc(c, rb);
+        P->w[q] = buf_alloc(c, rb);
+    }
+    P->dd = buf_alloc(c, sizeof(float) * n);
+    P->sinkbits = buf_alloc(c, sizeof(uint32_t) * ((n + 31) / 32));
+    P->seedbits = buf_alloc(c, sizeof(uint32_t) * ((n + 31) / 32));
+    P->agg = buf_alloc(c, sizeof(float) * (size_t)P->kt * nt * PPR_LANES);
+    P->first = buf_alloc(c, sizeof(float) * (size_t)P->kt * nt * PPR_LANES);
+    P->part_a = buf_alloc(c, sizeof(double) * 2 * (size_t)P->grid * S);
+    P->part_b = buf_alloc(c, sizeof(double) * 2 * (size_t)P->grid * S);
+    P->active = buf_alloc(c, sizeof(int32_t) * S);
+    P->iters = buf_alloc(c, sizeof(int32_t) * S);
+    P->itermax = buf_alloc(c, sizeof(int32_t) * S);
+    P->tol = buf_alloc(c, sizeof(double) * S);
+    P->resid = buf_alloc(c, sizeof(double) * S);
+    P->tele = buf_alloc(c, sizeof(float) * S);
+    DevBuf deg = buf_alloc(c, sizeof(int32_t) * n), pres = buf_alloc(c, (size_t)n);
+    for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->dd, &P->sinkbits, &P->seedbits, &P->agg,
+                      &P->first, &P->part_a, &P->part_b, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid,
+                      &P->tele, &deg, &pres})
+        if (!b->p) st = GRB_OUT_OF_MEMORY;
+    for (int q = 0; q < 2 && !st; ++q) {
+        st = cuda_check(c, cudaMemsetAsync(P->r[q].p, 0, rb, c->stream), "ppr init");
+        if (!st) st = cuda_check(c, cudaMemsetAsync(P->w[q].p, 0, rb, c->stream), "ppr init");
+    }
+    for (DevBuf* b : {&P->seedbits, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid, &P->tele})
+        if (!st) st = cuda_check(c, cudaMemsetAsync(b->p, 0, b->bytes, c->stream), "ppr init");
+    if (!st) {
+        c->stats.kernel_launches += 3;
+        st = cuda_check(c, launch_col_degree(c->stream, n, A->nnz, (const int32_t*)A->col_idx.p, (int32_t*)deg.p,
+                                             (uint8_t*)pres.p), "out-degree");
+        if (!st) st = cuda_check(c, launch_ppr_divisor(c->stream, (int32_t)n, (const int32_t*)deg.p, damping,
+                                                       (float*)P->dd.p, (uint32_t*)P->sinkbits.p), "divisor");
+        if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr init");
+    }
+    buf_free(c, deg);
+    buf_free(c, pres);
+    if (!st) st = upload_seeds(P);
+    if (st) {
+        ppr_destroy(P);
+        return st;
+    }
+    *out = reinterpret_cast<grb_ppr>(P);
+    return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_slots(grb_ppr Ph, int32_t* slots) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph || !slots) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    *slots = P->slots;
+    return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_set(grb_ppr Ph, int32_t slot, const int32_t* seeds, int64_t nseeds, double tol, int64_t itermax) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph || !seeds) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (slot < 0 || slot >= P->slots || nseeds < 1 || itermax < 0 || itermax > INT32_MAX) return GRB_INVALID_VALUE;
+    std::vector<int32_t> S(seeds, seeds + nseeds);
+    for (int32_t v : S)
+        if (v < 0 || v >= P->n) return GRB_INVALID_INDEX;
+    std::sort(S.begin(), S.end());
+    S.erase(std::unique(S.begin(), S.end()), S.end());
+    Ctx* c = P->c;
+    DevBuf ds = buf_alloc(c, sizeof(int32_t) * S.size());
+    if (!ds.p) return GRB_OUT_OF_MEMORY;
+    grb_info st = cuda_check(c, cudaMemcpyAsync(ds.p, S.data(), sizeof(int32_t) * S.size(), cudaMemcpyHostToDevice,
+                                                c->stream), "seeds");
+    PprInit a;
+    a.slot = slot;
+    a.nseeds = (int32_t)S.size();
+    a.nrows = (int32_t)P->n;
+    a.seeds = (const int32_t*)ds.p;
+    a.r0 = (float)(1.0 / (double)S.size());
+    a.r = (float*)P->r[P->cur].p;
+    a.w = (float*)P->w[P->cur].p;
+    a.dd = (const float*)P->dd.p;
+    a.sinkbits = (const uint32_t*)P->sinkbits.p;
+    a.tele_base = (float*)P->tele.p;
+    a.damping = P->damping;
+    if (!st) {
+        c->stats.kernel_launches += 2;
+        st = cuda_check(c, launch_ppr_init_slot(c->stream, a), "ppr slot init");
+    }
+    // the loop test before the first body: rdiff = 1 > tol
+    const int32_t act = (itermax > 0 && 1.0 > tol) ? 1 : 0, zero = 0, im = (int32_t)itermax;
+    const double one = 1.0;
+    struct { DevBuf* b; const void* v; size_t sz; } w[] = {
+        {&P->active, &act, 4}, {&P->iters, &zero, 4}, {&P->itermax, &im, 4}, {&P->tol, &tol, 8}, {&P->resid, &one, 8}};
+    for (auto& x : w)
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync((char*)x.b->p + x.sz * slot, x.v, x.sz, cudaMemcpyHostToDevice,
+                                               c->stream), "slot state");
+    // host values above must outlive the copies
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "slot state");
+    buf_free(c, ds);
+    if (st) return st;
+    P->seeds[slot] = std::move(S);
+    P->dirty = true;
+    return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_clear(grb_ppr Ph, int32_t slot) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (slot < 0 || slot >= P->slots) return GRB_INVALID_VALUE;
+    const int32_t zero = 0;
+    grb_info st = cuda_check(P->c, cudaMemcpyAsync((int32_t*)P->active.p + slot, &zero, 4, cudaMemcpyHostToDevice,
+                                                   P->c->stream), "slot clear");
+    if (!st) st = cuda_check(P->c, cudaStreamSynchronize(P->c->stream), "slot clear");
+    if (st) return st;
+    P->seeds[slot].clear();
+    P->dirty = true;
+    return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_run(grb_ppr Ph, int64_t iters) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (iters < 0 || iters > 100000) return GRB_INVALID_VALUE;
+    if (iters == 0) return GRB_SUCCESS;
+    Ctx* c = P->c;
+    grb_info st = GRB_SUCCESS;
+    if (P->dirty) st = upload_seeds(P);
+    if (st) return st;
+    if (!P->exec || P->exec_iters != iters || P->exec_cur != P->cur) {
+        drop_graph(P);
+        if (!c->capture_stream)
+            st = cuda_check(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t g = nullptr;
+        if (!st) st = cuda_check(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal),
+                                 "ppr capture");
+        if (!st) {
+            grb_info s1 = record_iterations(P, c->capture_stream, iters);
+            grb_info s2 = cuda_check(c, cudaStreamEndCapture(c->capture_stream, &g), "ppr capture");
+            st = s1 ? s1 : s2;
+        }
+        if (!st) st = cuda_check(c, cudaGraphInstantiate(&P->exec, g, 0), "ppr instantiate");
+        if (g) cudaGraphDestroy(g);
+        if (st) return st;
+        P->exec_iters = iters;
+        P->exec_cur = P->cur;
+    }
+    st = cuda_check(c, cudaGraphLaunch(P->exec, c->stream), "ppr launch");
+    if (st) return st;
+    c->stats.kernel_launches += 3 * iters;
+    P->cur = (int)((P->cur + iters) & 1);
+    return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_status(grb_ppr Ph, int32_t* active, int64_t* iters, double* resid) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    Ctx* c = P->c;
+    const int S = P->slots;
+    std::vector<int32_t> a(S), it(S);
+    std::vector<double> rs(S);
+    grb_info st = cuda_check(c, cudaMemcpyAsync(a.data(), P->active.p, 4 * S, cudaMemcpyDeviceToHost, c->stream),
+                             "ppr status");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(it.data(), P->iters.p, 4 * S, cudaMemcpyDeviceToHost, c->stream),
+                             "ppr status");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(rs.data(), P->resid.p, 8 * S, cudaMemcpyDeviceToHost, c->stream),
+                             "ppr status");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr status");
+    if (st) return st;
+    for (int s = 0; s < S; ++s) {
+        if (active) active[s] = a[s];
+        if (iters) iters[s] = it[s];
+        if (resid) resid[s] = rs[s];
+    }
+    return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_get(grb_ppr Ph, int32_t slot, float* ranks, int out_is_device) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph || !ranks) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (slot < 0 || slot >= P->slots) return GRB_INVALID_VALUE;
+    Ctx* c = P->c;
+    float* dst = ranks;
+    DevBuf tmp;
+    if (!out_is_device) {
+        tmp = buf_alloc(c, sizeof(float) * P->n);
+        if (!tmp.p) return GRB_OUT_OF_MEMORY;
+        dst = (float*)tmp.p;
+    }
+    c->stats.kernel_launches++;
+    grb_info st = cuda_check(c, launch_ppr_extract(c->stream, (int32_t)P->n, (const float*)P->r[P->cur].p, slot, dst),
+                             "ppr extract");
+    if (!st && !out_is_device)
+        st = cuda_check(c, cudaMemcpyAsync(ranks, tmp.p, sizeof(float) * P->n, cudaMemcpyDeviceToHost, c->stream),
+                        "ppr extract");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr extract");
+    buf_free(c, tmp);
+    return st;
+}
+
+}  // extern "C"
