@@ -347,6 +347,39 @@ grb_info grb_ppr_status(grb_ppr P, int32_t* active, int64_t* iters, double* resi
  * memory, or device memory when out_is_device).  Waits for the queued work. */
 grb_info grb_ppr_get(grb_ppr P, int32_t slot, float* ranks, int out_is_device);
 
+/* Serving loop (extension): answers a stream of personalised-PageRank
+ * queries by continuous batching on one grb_ppr.  Query q arrives
+ * arrival_s[q] seconds after the call starts (non-decreasing) with seeds
+ * seed_idx[seed_ptr[q] .. seed_ptr[q+1]) (at least one).  The loop admits
+ * every arrived query into a free slot, runs `chunk` bodies for all queries
+ * in flight, retires the finished ones and repeats, sleeping while idle.
+ * Slots: as many as mem_fraction of the free device memory holds (about
+ * 16 n bytes each), at most `slots` when slots > 0 and GRB_PPR_MAX_SLOTS;
+ * more arrivals than slots wait in arrival order.  A query's result is the
+ * one it gets alone (grb_ppr).  Returns when every query is answered. */
+typedef struct grb_serve_config {
+    double damping;
+    double tol;            /* each query's loop test: rdiff > tol */
+    int64_t itermax;
+    int64_t chunk;         /* bodies per scheduling step (>= 1) */
+    int32_t slots;         /* 0: limited by memory only */
+    double mem_fraction;   /* (0, 1] */
+} grb_serve_config;
+
+typedef struct grb_serve_result {
+    double* latency_s;     /* [nq] answer time - arrival time (caller-owned) */
+    int64_t* iters;        /* [nq] bodies run */
+    double* resid;         /* [nq] final rdiff */
+    float* ranks;          /* [nq * n] host ranks, or NULL to skip */
+    int32_t slots;         /* out: slots used */
+    int64_t steps;         /* out: scheduling steps (graph launches) */
+    int64_t max_in_flight; /* out */
+    double wall_s;         /* out: time from start to the last answer */
+} grb_serve_result;
+
+grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, const double* arrival_s,
+                       const int64_t* seed_ptr, const int32_t* seed_idx, grb_serve_result* out);
+
 /* ------------------------------------------------ allocation-free call */
 
 /* The paper has no counterpart to this call; it serves callers that cannot

@@ -65,6 +65,17 @@ class grb_stats(ctypes.Structure):
                                               "device_bytes", "cache_hits", "last_loop_kernel_ns")]
 
 
+class grb_serve_config(ctypes.Structure):
+    _fields_ = [("damping", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int64),
+                ("chunk", ctypes.c_int64), ("slots", ctypes.c_int32), ("mem_fraction", ctypes.c_double)]
+
+
+class grb_serve_result(ctypes.Structure):
+    _fields_ = [("latency_s", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("resid", ctypes.c_void_p),
+                ("ranks", ctypes.c_void_p), ("slots", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("max_in_flight", ctypes.c_int64), ("wall_s", ctypes.c_double)]
+
+
 def binop(code: int, k: float = 0.0) -> grb_binop:
     return grb_binop(int(code), 0, float(k))
 
@@ -126,6 +137,7 @@ def _declare(lib):
         "grb_ppr_run": [V, I64],
         "grb_ppr_status": [V, V, V, V],
         "grb_ppr_get": [V, ctypes.c_int32, V, I],
+        "grb_ppr_serve": [V, P(grb_serve_config), I64, V, V, V, P(grb_serve_result)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -159,7 +171,8 @@ def symbols():
                         "grb_mxv", "grb_ewise_add", "grb_ewise_mult", "grb_reduce", "grb_wait",
                         "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
                         "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc", "grb_ppr_new", "grb_ppr_slots",
-                        "grb_ppr_set", "grb_ppr_clear", "grb_ppr_run", "grb_ppr_status", "grb_ppr_get")
+                        "grb_ppr_set", "grb_ppr_clear", "grb_ppr_run", "grb_ppr_status", "grb_ppr_get",
+                        "grb_ppr_serve")
             if hasattr(lib, n)]
 
 
@@ -457,6 +470,35 @@ def grb_ppr_get(P: int, slot: int, n: int, out=None):
     r = np.empty(n, np.float32)
     _check(load().grb_ppr_get(P, int(slot), r.ctypes.data, 0), "grb_ppr_get")
     return r
+
+
+def grb_ppr_serve(AT: int, arrival_s, seed_sets, damping: float = 0.85, tol: float = 1e-6, itermax: int = 1000,
+                  chunk: int = 4, slots: int = 0, mem_fraction: float = 0.5, n: int | None = None,
+                  want_ranks: bool = False):
+    """Run the serving loop on host arrival times and seed sets.  Returns a
+    dict: latency_s, iters, resid (numpy, per query), ranks (nq x n float32
+    when want_ranks), slots, steps, max_in_flight, wall_s."""
+    arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    nq = len(arrival)
+    ptr = np.zeros(nq + 1, np.int64)
+    ptr[1:] = np.cumsum([len(s) for s in seed_sets])
+    idx = np.ascontiguousarray(np.concatenate([np.asarray(s, np.int32) for s in seed_sets]) if nq else
+                               np.zeros(1, np.int32), dtype=np.int32)
+    lat = np.zeros(nq, np.float64)
+    its = np.zeros(nq, np.int64)
+    res = np.zeros(nq, np.float64)
+    ranks = None
+    if want_ranks:
+        if n is None:
+            n = grb_matrix_nrows(AT)
+        ranks = np.zeros((nq, n), np.float32)
+    cfg = grb_serve_config(float(damping), float(tol), int(itermax), int(chunk), int(slots), float(mem_fraction))
+    out = grb_serve_result(lat.ctypes.data, its.ctypes.data, res.ctypes.data,
+                           ranks.ctypes.data if ranks is not None else None, 0, 0, 0, 0.0)
+    _check(load().grb_ppr_serve(AT, ctypes.byref(cfg), nq, arrival.ctypes.data, ptr.ctypes.data, idx.ctypes.data,
+                                ctypes.byref(out)), "grb_ppr_serve", AT)
+    return {"latency_s": lat, "iters": its, "resid": res, "ranks": ranks, "slots": out.slots, "steps": out.steps,
+            "max_in_flight": out.max_in_flight, "wall_s": out.wall_s}
 
 
 def grb_free(obj) -> None:

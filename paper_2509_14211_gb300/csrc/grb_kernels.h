@@ -306,6 +306,8 @@ struct PprFinish {
     const double* tol = nullptr;
     double* resid = nullptr;
     float* tele_base = nullptr;
+    int32_t* final_buf = nullptr;   // per slot: rank buffer of its last body
+    int32_t out_buf = 0;            // rank buffer this body writes
     double damping = 0.85;
     int64_t n = 0;
 };

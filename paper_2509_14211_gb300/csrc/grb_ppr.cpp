@@ -26,7 +26,7 @@ struct Ppr {
     int grid = 0;
     int cur = 0;                       // which of r[2] / w[2] holds the current iterate
     DevBuf r[2], w[2], dd, sinkbits, seedbits, agg, first, part_a, part_b;
-    DevBuf active, iters, itermax, tol, resid, tele;
+    DevBuf active, iters, itermax, tol, resid, tele, final_buf;
     DevBuf seed_ptr, seed_row, seed_lane, seed_val;
     std::vector<std::vector<int32_t>> seeds;
     bool dirty = true;
@@ -145,6 +145,7 @@ grb_info record_iterations(Ppr* P, cudaStream_t st, int64_t iters) {
     f.tol = (const double*)P->tol.p;
     f.resid = (double*)P->resid.p;
     f.tele_base = (float*)P->tele.p;
+    f.final_buf = (int32_t*)P->final_buf.p;
     f.damping = P->damping;
     f.n = P->n;
     cudaError_t e = cudaSuccess;
@@ -156,6 +157,7 @@ grb_info record_iterations(Ppr* P, cudaStream_t st, int64_t iters) {
             p.part = (double*)P->part_b.p;
             e = launch_ppr_fixups(st, p, P->grid);
         }
+        f.out_buf = (int32_t)((P->cur + k + 1) & 1);
         if (e == cudaSuccess) e = launch_ppr_finish(st, f);
     }
     return cuda_check(P->c, e, "ppr iteration");
@@ -169,7 +171,7 @@ void ppr_destroy(Ppr* P) {
     drop_graph(P);
     for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->dd, &P->sinkbits, &P->seedbits, &P->agg,
                       &P->first, &P->part_a, &P->part_b, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid,
-                      &P->tele, &P->seed_ptr, &P->seed_row, &P->seed_lane, &P->seed_val})
+                      &P->tele, &P->final_buf, &P->seed_ptr, &P->seed_row, &P->seed_lane, &P->seed_val})
         buf_free(c, *b);
     matrix_unref(P->A);
     P->kind = Kind::DEAD;
@@ -222,16 +224,17 @@ grb_info grb_ppr_new(grb_ppr* out, grb_matrix Am, double damping, int32_t slots)
     P->tol = buf_alloc(c, sizeof(double) * S);
     P->resid = buf_alloc(c, sizeof(double) * S);
     P->tele = buf_alloc(c, sizeof(float) * S);
+    P->final_buf = buf_alloc(c, sizeof(int32_t) * S);
     DevBuf deg = buf_alloc(c, sizeof(int32_t) * n), pres = buf_alloc(c, (size_t)n);
     for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->dd, &P->sinkbits, &P->seedbits, &P->agg,
                       &P->first, &P->part_a, &P->part_b, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid,
-                      &P->tele, &deg, &pres})
+                      &P->tele, &P->final_buf, &deg, &pres})
         if (!b->p) st = GRB_OUT_OF_MEMORY;
     for (int q = 0; q < 2 && !st; ++q) {
         st = cuda_check(c, cudaMemsetAsync(P->r[q].p, 0, rb, c->stream), "ppr init");
         if (!st) st = cuda_check(c, cudaMemsetAsync(P->w[q].p, 0, rb, c->stream), "ppr init");
     }
-    for (DevBuf* b : {&P->seedbits, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid, &P->tele})
+    for (DevBuf* b : {&P->seedbits, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid, &P->tele, &P->final_buf})
         if (!st) st = cuda_check(c, cudaMemsetAsync(b->p, 0, b->bytes, c->stream), "ppr init");
     if (!st) {
         c->stats.kernel_launches += 3;
@@ -292,10 +295,11 @@ grb_info grb_ppr_set(grb_ppr Ph, int32_t slot, const int32_t* seeds, int64_t nse
         st = cuda_check(c, launch_ppr_init_slot(c->stream, a), "ppr slot init");
     }
     // the loop test before the first body: rdiff = 1 > tol
-    const int32_t act = (itermax > 0 && 1.0 > tol) ? 1 : 0, zero = 0, im = (int32_t)itermax;
+    const int32_t act = (itermax > 0 && 1.0 > tol) ? 1 : 0, zero = 0, im = (int32_t)itermax, fb = P->cur;
     const double one = 1.0;
     struct { DevBuf* b; const void* v; size_t sz; } w[] = {
-        {&P->active, &act, 4}, {&P->iters, &zero, 4}, {&P->itermax, &im, 4}, {&P->tol, &tol, 8}, {&P->resid, &one, 8}};
+        {&P->active, &act, 4}, {&P->iters, &zero, 4}, {&P->itermax, &im, 4}, {&P->tol, &tol, 8}, {&P->resid, &one, 8},
+        {&P->final_buf, &fb, 4}};
     for (auto& x : w)
         if (!st)
             st = cuda_check(c, cudaMemcpyAsync((char*)x.b->p + x.sz * slot, x.v, x.sz, cudaMemcpyHostToDevice,
@@ -396,9 +400,19 @@ grb_info grb_ppr_get(grb_ppr Ph, int32_t slot, float* ranks, int out_is_device) 
         if (!tmp.p) return GRB_OUT_OF_MEMORY;
         dst = (float*)tmp.p;
     }
+    // an active slot's rank is in the current buffer; a finished one's where
+    // its last body left it
+    int32_t act = 0, fb = 0;
+    grb_info st = cuda_check(c, cudaMemcpyAsync(&act, (int32_t*)P->active.p + slot, 4, cudaMemcpyDeviceToHost,
+                                                c->stream), "ppr extract");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(&fb, (int32_t*)P->final_buf.p + slot, 4, cudaMemcpyDeviceToHost,
+                                                c->stream), "ppr extract");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr extract");
+    const int buf = act ? P->cur : (fb & 1);
     c->stats.kernel_launches++;
-    grb_info st = cuda_check(c, launch_ppr_extract(c->stream, (int32_t)P->n, (const float*)P->r[P->cur].p, slot, dst),
-                             "ppr extract");
+    if (!st)
+        st = cuda_check(c, launch_ppr_extract(c->stream, (int32_t)P->n, (const float*)P->r[buf].p, slot, dst),
+                        "ppr extract");
     if (!st && !out_is_device)
         st = cuda_check(c, cudaMemcpyAsync(ranks, tmp.p, sizeof(float) * P->n, cudaMemcpyDeviceToHost, c->stream),
                         "ppr extract");

@@ -73,20 +73,20 @@ __device__ __forceinline__ float seed_term(const PprParams& p, int kt, int i, in
 
 // Epilogue of row i for this lane's slot: r' = (seed + d D / n) + sum, the
 // next gather value, and the residual / dangling-mass terms.  A finished
-// (inactive) slot keeps its rank: r' = r.
+// (inactive) slot writes nothing: its last iterate stays in the buffer the
+// finish kernel recorded.
 __device__ __forceinline__ void ppr_row(const PprParams& p, int kt, int i, float sum, int lane, bool act, float tb,
                                         Kahan& res, Kahan& dang) {
+    const float sv = seed_term(p, kt, i, lane);   // uniform across the warp
+    if (!act) return;
     const size_t o = ((size_t)kt * (size_t)p.nrows + (size_t)i) * PPR_LANES + (size_t)lane;
     const float rold = __ldcs(p.r_old + o);
     const float dd = __ldg(p.dd + i);
-    const float sv = seed_term(p, kt, i, lane);
-    const float rn = act ? (sv + tb) + sum : rold;
+    const float rn = (sv + tb) + sum;
     __stcs(p.r_new + o, rn);
     p.w_new[o] = rn / dd;
-    if (act) {
-        res.add(fabsf(rold - rn));
-        if (bit_of(p.sinkbits, i)) dang.add(rn);
-    }
+    res.add(fabsf(rold - rn));
+    if (bit_of(p.sinkbits, i)) dang.add(rn);
 }
 
 // Per-CTA partials of every slot: the warps' accumulators folded in warp
@@ -177,6 +177,13 @@ __global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_tiles_kernel(const __grid_co
         Kahan res, dang;
         const bool act = __ldg(p.active + kt * PPR_LANES + lane) != 0;
         const float tb = __ldg(p.tele_base + kt * PPR_LANES + lane);
+        // a k-tile without an active slot is skipped (the same decision in
+        // every warp: all read the same flags)
+        if (!__any_sync(FULL, act)) {
+            sm.res[kt][warp][lane] = 0.0;
+            sm.dang[kt][warp][lane] = 0.0;
+            continue;
+        }
         for (int t = w0; t < p.ntiles; t += nwarps) ppr_tile(p, kt, t, lane, act, tb, res, dang);
         // rows without nonzeros: the epilogue with an empty sum
         for (int e = w0; e < p.n_empty; e += nwarps)
@@ -199,6 +206,11 @@ __global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_fixups_kernel(const __grid_c
         Kahan res, dang;
         const bool act = __ldg(p.active + kt * PPR_LANES + lane) != 0;
         const float tb = __ldg(p.tele_base + kt * PPR_LANES + lane);
+        if (!__any_sync(FULL, act)) {
+            sm.res[kt][warp][lane] = 0.0;
+            sm.dang[kt][warp][lane] = 0.0;
+            continue;
+        }
         for (int t = blockIdx.x * NW + warp; t < p.ntiles; t += nwarps) {
             const FixDesc f = p.fix[t];
             if (f.row < 0) continue;
@@ -241,7 +253,10 @@ __global__ void ppr_finish_kernel(const __grid_constant__ PprFinish f) {
         f.iters[s] = k;
         f.resid[s] = R;
         f.tele_base[s] = (float)(f.damping * D / (double)f.n);
-        if (!(R > f.tol[s]) || k >= f.itermax[s]) f.active[s] = 0;
+        if (!(R > f.tol[s]) || k >= f.itermax[s]) {
+            f.active[s] = 0;
+            f.final_buf[s] = f.out_buf;   // where this body left the slot's rank
+        }
     }
 }
 

@@ -1,0 +1,103 @@
+"""Serving loop (grb_ppr_serve): continuous batching of personalised-PageRank
+queries.  Every answer must equal the query's answer alone (bit for bit:
+slot arithmetic is independent of the other slots and of admission time)
+and match the FP64 oracle at its body count (L1 <= 1e-6)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from oracle import SparseVec
+
+pytestmark = pytest.mark.gpu
+D = 0.85
+
+
+@pytest.fixture(scope="module")
+def grb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2509_14211_gb300 as g
+
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def setup(grb):
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    n = 1 << 12
+    src, dst = graphgen.rmat_edges(12, 16, seed=4)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    yield n, src, dst, AT
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+
+
+def _alone(grb, AT, n, seeds, tol, itermax):
+    P = grb.grb_ppr_new(AT, D, 1)
+    try:
+        grb.grb_ppr_set(P, 0, seeds, tol, itermax)
+        while True:
+            grb.grb_ppr_run(P, 16)
+            act, its, res = grb.grb_ppr_status(P)
+            if not act[0]:
+                break
+        return grb.grb_ppr_get(P, 0, n), int(its[0])
+    finally:
+        grb.grb_free(P)
+
+
+def test_burst_with_queueing_matches_alone(grb, setup):
+    """80 queries -- 40 at once, then a Poisson stream at ~2000/s -- into 32
+    slots: queries queue, are admitted while others are mid-flight, and
+    still get their alone answer."""
+    n, src, dst, AT = setup
+    sets = graphgen.ppr_seed_sets(n, 80, 1, 64, seed=4, log_uniform=True)
+    arr = np.concatenate([np.zeros(40), 0.001 + graphgen.poisson_arrivals(2000.0, 40, seed=4)])
+    tol, itermax = 1e-7, 300
+    out = grb.grb_ppr_serve(AT, arr, sets, damping=D, tol=tol, itermax=itermax, chunk=3, slots=32,
+                            want_ranks=True)
+    assert out["slots"] == 32 and out["max_in_flight"] == 32
+    assert np.all(out["latency_s"] > 0) and np.all(out["resid"] <= tol) and np.all(out["iters"] < itermax)
+    for q in range(80):
+        r, it = _alone(grb, AT, n, sets[q], tol, itermax)
+        assert it == out["iters"][q]
+        assert np.array_equal(out["ranks"][q], r), q
+    ptr, col = oracle.build_at(n, src, dst)
+    od = oracle.out_degree(ptr, col)
+    for q in (0, 41, 79):
+        S = np.unique(sets[q])
+        ref, _, _ = oracle.pagerank(ptr, col, od, damping=D, tol=-1.0, itermax=int(out["iters"][q]), mode="uniform",
+                                    personal=SparseVec(n, S, np.full(len(S), 1.0 / len(S))))
+        assert np.sum(np.abs(out["ranks"][q].astype(np.float64) - ref)) <= 1e-6
+
+
+def test_sparse_arrivals_and_memory_admission(grb, setup):
+    """Queries spread out in time are answered one or two at a time; with no
+    slot limit the slot count comes from free memory (capped at 128)."""
+    n, _, _, AT = setup
+    sets = graphgen.ppr_seed_sets(n, 6, 1, 8, seed=9)
+    arr = np.arange(6) * 0.05
+    out = grb.grb_ppr_serve(AT, arr, sets, damping=D, tol=1e-6, itermax=200, chunk=4, slots=0)
+    assert out["slots"] == grb.GRB_PPR_MAX_SLOTS
+    assert out["max_in_flight"] <= 3
+    assert out["wall_s"] >= arr[-1]
+    assert np.all(out["iters"] > 0)
+
+
+def test_serve_argument_errors(grb, setup):
+    n, _, _, AT = setup
+    with pytest.raises(grb.GrbError) as e:
+        grb.grb_ppr_serve(AT, [0.2, 0.1], [[1], [2]])
+    assert e.value.code == grb.GRB_INVALID_VALUE
+    with pytest.raises(grb.GrbError) as e:
+        grb.grb_ppr_serve(AT, [0.0], [[]])
+    assert e.value.code == grb.GRB_INVALID_VALUE
+    with pytest.raises(grb.GrbError) as e:
+        grb.grb_ppr_serve(AT, [0.0], [[n]])
+    assert e.value.code == grb.GRB_INVALID_INDEX
