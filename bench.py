@@ -217,6 +217,77 @@ def run_mixed_leg(grb, torch, stream):
     return out
 
 
+def run_ppr_leg(grb, torch, stream):
+    """Batched personalised PageRank: R-MAT scale 20, 64 queries with 1-32
+    uniformly drawn seeds (seed 3), 50 bodies, as one slot batch (SpMM over
+    64 right-hand sides).  CUDA events around the enqueued CUDA graph."""
+    import graphgen
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    n, k, iters = 1 << 20, 64, 50
+    src, dst = graphgen.rmat_edges(20, 16, seed=3)
+    sets = graphgen.ppr_seed_sets(n, k, 1, 32, seed=3)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    m = grb.grb_matrix_nvals(AT)
+    P = grb.grb_ppr_new(AT, DAMPING, k)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for rep in range(4):
+        for s, S in enumerate(sets):
+            grb.grb_ppr_set(P, s, S, -1.0, iters)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        grb.grb_ppr_run(P, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:                       # the first run captures the graph
+            times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[len(times) // 2]
+    out = {"workload": "R-MAT scale 20 (1,048,576 vertices, edge factor 16, seed 3), 64 personalised queries with "
+                       "1-32 uniform seeds each, FP32, 50 bodies, uniform dangling",
+           "n": n, "m": m, "k": k, "bodies": iters, "ms": ms, "ms_per_body": ms / iters,
+           "edge_query_updates_per_s_G": m * k * iters / (ms * 1e-3) / 1e9,
+           "algorithmic_bytes_per_body": 4 * m + 4 * (n + 1) + 4 * k * 4 * n}
+    out["hbm_frac_of_measured"] = out["algorithmic_bytes_per_body"] / (out["ms_per_body"] * 1e-3) / 1e9 / _peaks()[0]
+    grb.grb_free(P)
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+    return out
+
+
+def run_serve_leg(grb):
+    """Serving: R-MAT scale 24 resident on the device, Poisson query streams
+    (seed 4) with 1-64 log-uniform seeds, FP32 ranks with FP64 residual to an
+    L1 change of 1e-6, continuous batching in up to 128 slots."""
+    import graphgen
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    n = 1 << 24
+    src, dst = graphgen.rmat_edges(24, 16, seed=4)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    del src, dst
+    m = grb.grb_matrix_nvals(AT)
+    out = {"workload": "R-MAT scale 24 (16,777,216 vertices, edge factor 16, seed 4); queries with 1-64 log-uniform "
+                       "seeds; stop at L1 change 1e-6; chunk of 4 bodies per scheduling step",
+           "n": n, "m": m, "levels": []}
+    for rate, count in ((10.0, 24), (200.0, 128), (2000.0, 128)):
+        sets = graphgen.ppr_seed_sets(n, count, 1, 64, seed=4, log_uniform=True)
+        arr = graphgen.poisson_arrivals(rate, count, seed=4)
+        r = grb.grb_ppr_serve(AT, arr, sets, damping=DAMPING, tol=1e-6, itermax=1000, chunk=4, slots=0,
+                              mem_fraction=0.5)
+        lat = r["latency_s"]
+        out["levels"].append({"offered_qps": rate, "queries": count, "answered_qps": count / r["wall_s"],
+                              "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                              "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                              "mean_bodies": float(np.mean(r["iters"])), "slots": r["slots"],
+                              "max_in_flight": int(r["max_in_flight"]), "steps": int(r["steps"])})
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +296,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the FP64 oracle (error and CPU baseline)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision Erdos-Renyi 2^24 leg")
+    ap.add_argument("--no-ppr", action="store_true", help="skip the batched personalised PageRank leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="profiling run: only the fused device loop, on --scale/--iters (no JSON contract)")
     ap.add_argument("--scale", type=int, default=SCALE)
@@ -390,6 +463,8 @@ def main():
     grb.grb_free(ctx)
 
     mixed_leg = run_mixed_leg(grb, torch, stream) if not args.no_mixed else None
+    ppr_leg = run_ppr_leg(grb, torch, stream) if not args.no_ppr else None
+    serve_leg = run_serve_leg(grb) if not args.no_serve else None
 
     # ---------------------------------------------------------- roofline
     # algorithmic bytes of one launch of the persistent kernel: per body
@@ -430,6 +505,8 @@ def main():
         "fused_vs_unfused": unfused_ms / ms,
         "residual_after_50": rdiff,
         "mixed_er24": mixed_leg,
+        "batched_ppr_rmat20_k64": ppr_leg,
+        "serving_rmat24": serve_leg,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and not args.no_oracle:
