@@ -380,6 +380,40 @@ typedef struct grb_serve_result {
 grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, const double* arrival_s,
                        const int64_t* seed_ptr, const int32_t* seed_idx, grb_serve_result* out);
 
+/* -------------------------------- batch of independent graphs (extension)
+ *
+ * Many PageRank problems on graphs of uneven size solved together.  AT is
+ * one block-diagonal A^T (grb_matrix_build_csr with TRANSPOSE over the
+ * graphs' edges, vertex ids offset so that graph g owns vertices
+ * vptr[g] .. vptr[g+1]-1); an edge between two graphs is an error.  Every
+ * graph runs the §IV loop with uniform dangling on its own (r_0 = 1/n_g,
+ * teleport (1-d)/n_g + d D_g / n_g, FP64 residual, its own loop test); FP32
+ * ranks.  A body is one launch over all graphs; a solve is captured as a
+ * CUDA graph.  The launch shape (resident CTAs per SM) is picked by an
+ * autotuner that times each candidate on the batch (grb_prbatch_tune, or
+ * automatically before the first run); results do not depend on it. */
+typedef struct grb_prbatch_s* grb_prbatch;
+
+/* vptr: host, ngraphs + 1 non-decreasing offsets with vptr[0] = 0,
+ * vptr[ngraphs] = nrows(AT), every graph at least one vertex.  Holds a
+ * reference to AT.  Errors: GRB_INVALID_VALUE (bad offsets, non-square or
+ * valued matrix, an edge across graphs, damping outside [0, 1)). */
+grb_info grb_prbatch_new(grb_prbatch* B, grb_matrix AT, int32_t ngraphs, const int64_t* vptr, double damping);
+
+/* Autotune: time trial_bodies (1..1000) bodies for every candidate count of
+ * resident CTAs per SM; ms_per_body[q] (host, cap entries, optional) gets
+ * the time for q+1 CTAs per SM, *chosen (optional) the winner. */
+grb_info grb_prbatch_tune(grb_prbatch B, int64_t trial_bodies, double* ms_per_body, int32_t cap, int32_t* chosen);
+
+/* Solve every graph from its start vector: `while iter <= itermax &&
+ * rdiff > tol` per graph, bodies launched `chunk` at a time until no graph's
+ * loop goes on.  Blocks until done. */
+grb_info grb_prbatch_run(grb_prbatch B, double tol, int64_t itermax, int64_t chunk);
+
+/* ranks (host, nrows floats, optional): every graph's rank at its vertex
+ * offsets; iters / resid (host, ngraphs, optional): bodies run, last rdiff. */
+grb_info grb_prbatch_result(grb_prbatch B, float* ranks, int64_t* iters, double* resid);
+
 /* ------------------------------------------------ allocation-free call */
 
 /* The paper has no counterpart to this call; it serves callers that cannot

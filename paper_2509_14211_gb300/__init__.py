@@ -138,6 +138,10 @@ def _declare(lib):
         "grb_ppr_status": [V, V, V, V],
         "grb_ppr_get": [V, ctypes.c_int32, V, I],
         "grb_ppr_serve": [V, P(grb_serve_config), I64, V, V, V, P(grb_serve_result)],
+        "grb_prbatch_new": [P(V), V, ctypes.c_int32, V, D],
+        "grb_prbatch_tune": [V, I64, V, ctypes.c_int32, V],
+        "grb_prbatch_run": [V, D, I64, I64],
+        "grb_prbatch_result": [V, V, V, V],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -172,7 +176,8 @@ def symbols():
                         "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
                         "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc", "grb_ppr_new", "grb_ppr_slots",
                         "grb_ppr_set", "grb_ppr_clear", "grb_ppr_run", "grb_ppr_status", "grb_ppr_get",
-                        "grb_ppr_serve")
+                        "grb_ppr_serve", "grb_prbatch_new", "grb_prbatch_tune", "grb_prbatch_run",
+                        "grb_prbatch_result")
             if hasattr(lib, n)]
 
 
@@ -499,6 +504,46 @@ def grb_ppr_serve(AT: int, arrival_s, seed_sets, damping: float = 0.85, tol: flo
                                 ctypes.byref(out)), "grb_ppr_serve", AT)
     return {"latency_s": lat, "iters": its, "resid": res, "ranks": ranks, "slots": out.slots, "steps": out.steps,
             "max_in_flight": out.max_in_flight, "wall_s": out.wall_s}
+
+
+# ------------------------------------------------ batch of independent graphs
+def block_diagonal_edges(graphs):
+    """Concatenate per-graph (n_g, src, dst) edge lists into one COO with
+    vertex ids offset per graph; returns (n_total, src, dst, vptr)."""
+    vptr = np.zeros(len(graphs) + 1, np.int64)
+    vptr[1:] = np.cumsum([g[0] for g in graphs])
+    src = np.concatenate([np.asarray(g[1], np.int64) + vptr[k] for k, g in enumerate(graphs)]).astype(np.int32)
+    dst = np.concatenate([np.asarray(g[2], np.int64) + vptr[k] for k, g in enumerate(graphs)]).astype(np.int32)
+    return int(vptr[-1]), src, dst, vptr
+
+
+def grb_prbatch_new(AT: int, vptr, damping: float = 0.85) -> int:
+    vptr = np.ascontiguousarray(vptr, dtype=np.int64)
+    out = ctypes.c_void_p()
+    _check(load().grb_prbatch_new(ctypes.byref(out), AT, len(vptr) - 1, vptr.ctypes.data, float(damping)),
+           "grb_prbatch_new", AT)
+    return out.value
+
+
+def grb_prbatch_tune(B: int, trial_bodies: int = 3):
+    """(ms per body for 1..k resident CTAs per SM, chosen CTAs per SM)."""
+    ms = np.zeros(16, np.float64)
+    ch = ctypes.c_int32()
+    _check(load().grb_prbatch_tune(B, int(trial_bodies), ms.ctypes.data, 16, ctypes.byref(ch)), "grb_prbatch_tune")
+    return ms[ms > 0], ch.value
+
+
+def grb_prbatch_run(B: int, tol: float, itermax: int, chunk: int = 16) -> None:
+    _check(load().grb_prbatch_run(B, float(tol), int(itermax), int(chunk)), "grb_prbatch_run")
+
+
+def grb_prbatch_result(B: int, n: int, ngraphs: int):
+    """(ranks float32[n], iters int64[ngraphs], resid float64[ngraphs])."""
+    r = np.empty(n, np.float32)
+    it = np.empty(ngraphs, np.int64)
+    rs = np.empty(ngraphs, np.float64)
+    _check(load().grb_prbatch_result(B, r.ctypes.data, it.ctypes.data, rs.ctypes.data), "grb_prbatch_result")
+    return r, it, rs
 
 
 def grb_free(obj) -> None:

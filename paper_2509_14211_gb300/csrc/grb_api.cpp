@@ -883,6 +883,8 @@ grb_info grb_free(void** obj) {
         matrix_unref(A);
     } else if (k == Kind::PPR) {
         ppr_destroy(reinterpret_cast<Ppr*>(*obj));
+    } else if (k == Kind::PRBATCH) {
+        prbatch_destroy(reinterpret_cast<PrBatch*>(*obj));
     } else if (k == Kind::CONTEXT) {
         Ctx* c = reinterpret_cast<Ctx*>(*obj);
         cudaStreamSynchronize(c->stream);

@@ -23,7 +23,7 @@
 
 namespace grb {
 
-enum class Kind : uint32_t { CONTEXT = 0x47524230u, MATRIX, VECTOR, SCALAR, PPR, DEAD = 0xDEADDEADu };
+enum class Kind : uint32_t { CONTEXT = 0x47524230u, MATRIX, VECTOR, SCALAR, PPR, PRBATCH, DEAD = 0xDEADDEADu };
 
 struct Ctx;
 struct Node;
@@ -231,6 +231,8 @@ grb_info ensure_relabel(Ctx* c, Matrix* A);
 grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits);
 struct Ppr;
 void ppr_destroy(Ppr* P);
+struct PrBatch;
+void prbatch_destroy(PrBatch* B);
 grb_info read_status(Ctx* c);
 PrParams plan_params_of(Ctx* c, Matrix* A);
 int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n = 0);

@@ -171,6 +171,50 @@ struct PrParams {
     // persistent loop: gathers of columns < hot_n are served from a copy of
     // w[0, hot_n) in shared memory (multiple of 4; 0 = off; FP32 only)
     int32_t hot_n = 0;
+    // batch of independent graphs (block-diagonal A^T): per-row graph id,
+    // per-graph loop state and teleport, per-row residual / dangling terms
+    const int32_t* graph_of = nullptr;
+    const int32_t* g_active = nullptr;
+    const float* g_tele = nullptr;
+    float* row_res = nullptr;
+    float* row_dang = nullptr;
+};
+
+// Per-graph fold of a batch body: one CTA per graph sums the rows' residual
+// and dangling terms in a fixed order, counts the body, applies the graph's
+// loop test and sets its next teleport (1-d)/n_g + d D_g / n_g.
+struct MgFinish {
+    int32_t ngraphs = 0;
+    const int64_t* vptr = nullptr;     // ngraphs + 1 row offsets
+    const float* row_res = nullptr;
+    const float* row_dang = nullptr;
+    int32_t* active = nullptr;
+    int32_t* iters = nullptr;
+    int32_t itermax = 0;
+    double tol = 0.0;
+    double* resid = nullptr;
+    float* tele = nullptr;
+    int32_t* final_buf = nullptr;
+    int32_t out_buf = 0;
+    double damping = 0.85;
+};
+
+// Start state of every graph of a batch: r = 1/n_g, w = r ./ d, the first
+// teleport from the dangling mass of r, active = (itermax > 0 && 1 > tol).
+struct MgInit {
+    int32_t ngraphs = 0;
+    const int64_t* vptr = nullptr;
+    const float* dd = nullptr;
+    const uint32_t* sinkbits = nullptr;
+    float* r = nullptr;
+    float* w = nullptr;
+    int32_t* active = nullptr;
+    int32_t* iters = nullptr;
+    double* resid = nullptr;
+    float* tele = nullptr;
+    int32_t* final_buf = nullptr;
+    int32_t start_active = 1;
+    double damping = 0.85;
 };
 
 // --------------------------------------------------------------- launchers
@@ -338,6 +382,19 @@ cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32
 cudaError_t launch_ppr_divisor(cudaStream_t st, int32_t n, const int32_t* deg, double damping, float* dd,
                                uint32_t* sinkbits);
 int ppr_blocks_per_sm();
+
+// One body of a batch of graphs: phase A, grid barrier, phase B over the
+// block-diagonal A^T; reads rbuf[from]/wbuf[from], writes the other pair
+// (cooperative launch of grid CTAs).
+cudaError_t launch_pr_batch(cudaStream_t st, const PrParams& p, int from, int grid);
+int pr_batch_blocks_per_sm();
+cudaError_t launch_mg_finish(cudaStream_t st, const MgFinish& f);
+cudaError_t launch_mg_init(cudaStream_t st, const MgInit& a);
+// graph_of[i] = g for vptr[g] <= i < vptr[g+1]; *bad (device) += rows with
+// a column outside their block.
+cudaError_t launch_mg_graph_of(cudaStream_t st, int32_t ngraphs, const int64_t* vptr, int32_t n,
+                               const int32_t* row_ptr, const int32_t* col_idx, int32_t* graph_of,
+                               unsigned long long* bad);
 
 // Resident CTAs per SM of the fused kernel for the given rank / gather types
 // (hot_n > 0: the persistent kernel with a hot copy of hot_n entries; 0 when

@@ -217,8 +217,15 @@ struct RowIn {
     uint32_t sinkword;
 };
 
-template <class T, class G, bool NC, bool LEAN>
+// Epilogue kinds: the general one (any fused group), the PageRank loop body
+// (scalar teleport, residual and next gather value always produced), and
+// the loop body of a batch of independent graphs (per-graph teleport and
+// loop state, per-row residual / dangling terms folded per graph later).
+enum : int { EPI_GEN = 0, EPI_LEAN = 1, EPI_MG = 2 };
+
+template <class T, class G, bool NC, int EPI>
 __device__ __forceinline__ RowIn<T> row_inputs(const PrParams& p, const TileIO<T, G>& io, int i) {
+    constexpr bool LEAN = EPI != EPI_GEN;
     RowIn<T> in;
     in.rold = (T)0;
     in.dd = (T)1;
@@ -231,11 +238,24 @@ __device__ __forceinline__ RowIn<T> row_inputs(const PrParams& p, const TileIO<T
 
 // Everything a finished row produces: the output value, its presence, the
 // next gather value, and its residual / dangling-mass contributions.
-template <class T, class G, bool LEAN>
+template <class T, class G, int EPI>
 __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, G>& io, int i, T s, bool nonempty,
                                              const RowIn<T>& in, Acc<T>& resid, Acc<T>& dang) {
     T v;
-    if (LEAN) {
+    if constexpr (EPI == EPI_MG) {
+        // row i of graph g: nothing once g's loop has ended (its rank stays
+        // in the buffer its last body wrote)
+        const int g = __ldg(p.graph_of + i);
+        if (!__ldg(p.g_active + g)) return;
+        const T tg = (T)__ldg(p.g_tele + g);
+        v = nonempty ? tg + s : tg;
+        io.out[i] = v;
+        gstore<G>(io.w_next, i, (float)(v / in.dd));
+        p.row_res[i] = (float)abs_c<T>(in.rold - v);
+        p.row_dang[i] = ((in.sinkword >> (i & 31)) & 1u) ? (float)v : 0.f;
+        return;
+    }
+    if (EPI == EPI_LEAN) {
         v = nonempty ? io.tele + s : io.tele;
         io.out[i] = v;
         resid.add(abs_c<T>(in.rold - v));
@@ -322,7 +342,7 @@ __device__ __forceinline__ TilePre tile_pre(const PrParams& p, int t, uint32_t m
     return f;
 }
 
-template <class T, class G, int GMODE, bool NC, bool LEAN, bool HOT = false>
+template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false>
 __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io,
                                           Acc<T>& resid, Acc<T>& dang, WarpSmem<T>& ws) {
     static_assert(PR_NZLANE == 8, "two 16-byte column loads per lane");
@@ -341,7 +361,7 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePr
     pre.sinkword = 0;
     if (f.pre_i >= 0) {
         pre_i = f.pre_i;
-        pre = row_inputs<T, G, NC, LEAN>(p, io, pre_i);
+        pre = row_inputs<T, G, NC, EPI>(p, io, pre_i);
     }
     const int cols[PR_NZLANE] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
     T v[PR_NZLANE];
@@ -389,29 +409,29 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePr
 
     // ---- epilogue of the rows finished here (row x on lane x % 32)
     if (x_lo == 1 && nrows > 0 && lane == 0) reinterpret_cast<T*>(p.first)[t] = ws.rowsum[0];
-    if (lane >= x_lo && lane < nrows) row_epilogue<T, G, LEAN>(p, io, pre_i, ws.rowsum[lane], true, pre, resid, dang);
+    if (lane >= x_lo && lane < nrows) row_epilogue<T, G, EPI>(p, io, pre_i, ws.rowsum[lane], true, pre, resid, dang);
     for (int x = 32 + lane; x < nrows; x += 32) {
         const int i = ld_stream(p.ne_rows + rfirst + x);
-        const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, i);
-        row_epilogue<T, G, LEAN>(p, io, i, ws.rowsum[x], true, in, resid, dang);
+        const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, i);
+        row_epilogue<T, G, EPI>(p, io, i, ws.rowsum[x], true, in, resid, dang);
     }
     __syncwarp();
 }
 
 // Rows without nonzeros: the epilogue with an empty sum.
-template <class T, class G, bool NC, bool LEAN>
+template <class T, class G, bool NC, int EPI>
 __device__ __forceinline__ void empty_rows(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
     const int nthreads = gridDim.x * blockDim.x;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.n_empty; e += nthreads) {
         const int i = ld_stream(p.empty_rows + e);
-        const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, i);
-        row_epilogue<T, G, LEAN>(p, io, i, (T)0, false, in, resid, dang);
+        const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, i);
+        row_epilogue<T, G, EPI>(p, io, i, (T)0, false, in, resid, dang);
     }
 }
 
 // Phase B: rows split across tiles.  Each thread takes tiles with a short
 // fixup (at most PR_LONG carries to add); each warp takes a long one.
-template <class T, class G, bool NC, bool LEAN>
+template <class T, class G, bool NC, int EPI>
 __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
     const T* agg = reinterpret_cast<const T*>(p.agg);
     const T* first = reinterpret_cast<const T*>(p.first);
@@ -419,11 +439,11 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p.ntiles; t += nthreads) {
         const FixDesc f = p.fix[t];
         if (f.row < 0 || t - f.ts > PR_LONG) continue;
-        const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, f.row);
+        const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, f.row);
         T sum = (T)0;
         for (int tt = f.ts; tt < t; ++tt) sum += __ldcg(agg + tt);
         sum += __ldcg(first + t);
-        row_epilogue<T, G, LEAN>(p, io, f.row, sum, true, in, resid, dang);
+        row_epilogue<T, G, EPI>(p, io, f.row, sum, true, in, resid, dang);
     }
     // rows spanning many tiles (hubs): one warp each, FP64 partial sums
     const int lane = threadIdx.x & 31;
@@ -438,15 +458,15 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(FULLMASK, sum, off);
         if (lane == 0) {
             sum += (double)__ldcg(first + t);
-            const RowIn<T> in = row_inputs<T, G, NC, LEAN>(p, io, f.row);
-            row_epilogue<T, G, LEAN>(p, io, f.row, (T)sum, true, in, resid, dang);
+            const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, f.row);
+            row_epilogue<T, G, EPI>(p, io, f.row, (T)sum, true, in, resid, dang);
         }
     }
 }
 
 // Phase A over the tiles of this warp (static assignment, next tile's
 // coordinates prefetched).
-template <class T, class G, int GMODE, bool NC, bool LEAN, bool HOT = false, int NW = NWARP>
+template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false, int NW = NWARP>
 __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
                                         Smem<T, NW>& sm) {
     const int warp = threadIdx.x >> 5;
@@ -465,9 +485,9 @@ __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& i
             meta2 = t1 + nwarps < p.ntiles ? __ldg(p.tile_meta + t1 + nwarps) : 0u;
             f = tile_pre(p, t1, m1);
         }
-        warp_tile<T, G, GMODE, NC, LEAN, HOT>(p, t, cur, io, resid, dang, sm.w[warp]);
+        warp_tile<T, G, GMODE, NC, EPI, HOT>(p, t, cur, io, resid, dang, sm.w[warp]);
     }
-    empty_rows<T, G, NC, LEAN>(p, io, resid, dang);
+    empty_rows<T, G, NC, EPI>(p, io, resid, dang);
 }
 
 template <class T>
@@ -512,9 +532,9 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
     io.w32_next = nullptr;
     io.phase32 = 0;
     Acc<T> racc, dacc;
-    phase_a<T, G, GMODE, true, LEAN>(p, io, racc, dacc, sm);
+    phase_a<T, G, GMODE, true, LEAN ? EPI_LEAN : EPI_GEN>(p, io, racc, dacc, sm);
     if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
-    fixups<T, G, true, LEAN>(p, io, racc, dacc);
+    fixups<T, G, true, LEAN ? EPI_LEAN : EPI_GEN>(p, io, racc, dacc);
     const double resid = block_sum_d<PR_BLOCK>(racc.value(), sm.red);
     const double dang = block_sum_d<PR_BLOCK>(dacc.value(), sm.red2);
     if (threadIdx.x == 0) {
@@ -606,9 +626,9 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
             __syncthreads();
         }
         Acc<T> racc, dacc;
-        phase_a<T, G, G_W, false, true, HOT, BLK / 32>(p, io, racc, dacc, sm);
+        phase_a<T, G, G_W, false, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
-        fixups<T, G, false, true>(p, io, racc, dacc);
+        fixups<T, G, false, EPI_LEAN>(p, io, racc, dacc);
         const double resid = block_sum_d<BLK>(racc.value(), sm.red);
         dang = block_sum_d<BLK>(dacc.value(), sm.red2);
         double* part = p.part + 2 * G_ * ((it + 1) & 1);
@@ -677,6 +697,89 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
         *p.iters_done = it;
         if (p.mixed_phase) *p.mixed_phase = phase32;
         p.sync->launch += 1;
+    }
+}
+
+// One body of a batch of independent graphs (block-diagonal A^T): the same
+// tiles, barrier and fixups as a PageRank body, with the per-graph epilogue.
+// The per-graph folds run in mg_finish_kernel (a kernel boundary away).
+__global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_batch_kernel(const __grid_constant__ PrParams p) {
+    __shared__ Smem<float> sm;
+    const int from = p.iter_index & 1;
+    TileIO<float, float> io{};
+    io.r_old = reinterpret_cast<const float*>(p.rbuf[from]);
+    io.out = reinterpret_cast<float*>(p.rbuf[from ^ 1]);
+    io.w = reinterpret_cast<const float*>(p.wbuf[from]);
+    io.w_next = reinterpret_cast<float*>(p.wbuf[from ^ 1]);
+    Acc<float> racc, dacc;
+    phase_a<float, float, G_W, true, EPI_MG>(p, io, racc, dacc, sm);
+    if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
+    fixups<float, float, true, EPI_MG>(p, io, racc, dacc);
+}
+
+constexpr int MG_BLOCK = 256;
+
+__global__ void __launch_bounds__(MG_BLOCK) mg_finish_kernel(const __grid_constant__ MgFinish f) {
+    __shared__ double red[MG_BLOCK / 32], red2[MG_BLOCK / 32];
+    const int g = blockIdx.x;
+    if (!f.active[g]) return;   // the same in the whole CTA
+    const int64_t lo = f.vptr[g], hi = f.vptr[g + 1];
+    double R = 0.0, D = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += MG_BLOCK) {
+        R += (double)f.row_res[i];
+        D += (double)f.row_dang[i];
+    }
+    R = block_sum_d<MG_BLOCK>(R, red);
+    D = block_sum_d<MG_BLOCK>(D, red2);
+    if (threadIdx.x == 0) {
+        const int32_t k = f.iters[g] + 1;
+        const double ng = (double)(hi - lo);
+        f.iters[g] = k;
+        f.resid[g] = R;
+        f.tele[g] = (float)((1.0 - f.damping) / ng + f.damping * D / ng);
+        if (!(R > f.tol) || k >= f.itermax) {
+            f.active[g] = 0;
+            f.final_buf[g] = f.out_buf;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MG_BLOCK) mg_init_kernel(const __grid_constant__ MgInit a) {
+    __shared__ double red[MG_BLOCK / 32];
+    const int g = blockIdx.x;
+    const int64_t lo = a.vptr[g], hi = a.vptr[g + 1];
+    const double ng = (double)(hi - lo);
+    const float r0 = (float)(1.0 / ng);
+    double D = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += MG_BLOCK) {
+        a.r[i] = r0;
+        a.w[i] = r0 / a.dd[i];
+        if ((a.sinkbits[i >> 5] >> (i & 31)) & 1u) D += (double)r0;
+    }
+    D = block_sum_d<MG_BLOCK>(D, red);
+    if (threadIdx.x == 0) {
+        a.active[g] = a.start_active;
+        a.iters[g] = 0;
+        a.resid[g] = 1.0;
+        a.final_buf[g] = 0;
+        a.tele[g] = (float)((1.0 - a.damping) / ng + a.damping * D / ng);
+    }
+}
+
+__global__ void mg_graph_of_kernel(int32_t ngraphs, const int64_t* vptr, int32_t n, const int32_t* row_ptr,
+                                   const int32_t* col_idx, int32_t* graph_of, unsigned long long* bad) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = ngraphs;   // last g with vptr[g] <= i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (vptr[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        graph_of[i] = lo;
+        const int64_t b = vptr[lo], e = vptr[lo + 1];
+        bool out = false;
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) out |= col_idx[k] < b || col_idx[k] >= e;
+        if (out) atomicAdd(bad, 1ull);
     }
 }
 
@@ -755,6 +858,41 @@ void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn) {
 }
 
 }  // namespace
+
+int pr_batch_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pr_batch_kernel, PR_BLOCK, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_pr_batch(cudaStream_t st, const PrParams& p0, int from, int grid) {
+    PrParams p = p0;
+    p.iter_index = from;
+    return coop_launch(pr_batch_kernel, grid, st, p);
+}
+
+cudaError_t launch_mg_finish(cudaStream_t st, const MgFinish& f) {
+    if (f.ngraphs <= 0) return cudaSuccess;
+    mg_finish_kernel<<<f.ngraphs, MG_BLOCK, 0, st>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_init(cudaStream_t st, const MgInit& a) {
+    if (a.ngraphs <= 0) return cudaSuccess;
+    mg_init_kernel<<<a.ngraphs, MG_BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_graph_of(cudaStream_t st, int32_t ngraphs, const int64_t* vptr, int32_t n,
+                               const int32_t* row_ptr, const int32_t* col_idx, int32_t* graph_of,
+                               unsigned long long* bad) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    int grid = (n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    mg_graph_of_kernel<<<grid, 256, 0, st>>>(ngraphs, vptr, n, row_ptr, col_idx, graph_of, bad);
+    return cudaGetLastError();
+}
 
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n) {
     int block = PR_BLOCK;
