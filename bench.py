@@ -256,6 +256,71 @@ def run_ppr_leg(grb, torch, stream):
     return out
 
 
+def run_batch_leg(grb, torch, stream):
+    """512 independent R-MAT graphs (scale 8-16, edge factor 8-32, seed 3) as
+    one block-diagonal batch: autotuned launch shape, 50 bodies captured in
+    one CUDA graph; beside it the same graphs solved one after another with
+    the single-graph persistent loop."""
+    import graphgen
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
+
+    specs = graphgen.batch_graph_specs(512, 8, 16, 8, 32, seed=3)
+    graphs = []
+    for scale, ef, s in specs:
+        src, dst = graphgen.rmat_edges(scale, ef, seed=s)
+        graphs.append((1 << scale, src, dst))
+    n, src, dst, vptr = grb.block_diagonal_edges(graphs)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    m = grb.grb_matrix_nvals(AT)
+    B = grb.grb_prbatch_new(AT, vptr, DAMPING)
+    tune_ms, chosen = grb.grb_prbatch_tune(B, 3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    grb.grb_prbatch_run(B, -1.0, ITERS, ITERS)           # warm-up (captures the graph)
+    times = []
+    for _ in range(3):
+        e0.record(stream)
+        grb.grb_prbatch_run(B, -1.0, ITERS, ITERS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[1]
+    grb.grb_prbatch_run(B, MIXED_TOL, 1000, 16)
+    _, its, _ = grb.grb_prbatch_result(B, n, len(graphs))
+    out = {"workload": "512 R-MAT graphs, scale 8-16, edge factor 8-32 (seed 3), FP32, uniform dangling, 50 bodies "
+                       "in one CUDA-graph launch", "graphs": len(graphs), "n": n, "m": m,
+           "autotune_ms_per_body_by_ctas_per_sm": [round(float(x), 4) for x in tune_ms],
+           "chosen_ctas_per_sm": chosen, "ms": ms, "gteps": m * ITERS / (ms * 1e-3) / 1e9,
+           "bodies_to_l1_change_1.76e-7": {"min": int(its.min()), "median": float(np.median(its)),
+                                           "max": int(its.max())}}
+    grb.grb_free(B)
+    grb.grb_free(AT)
+    # one graph at a time through the single-graph device loop
+    mats, probs = [], []
+    for ng, s_, d_ in graphs:
+        A1 = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, ng, ng, s_, d_, None, BUILD_FLAGS)
+        mats.append(A1)
+        probs.append(PageRankProblem(ctx, A1, ng, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform"))
+    for P1 in probs:
+        P1.run(-1.0, ITERS, "device")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for P1 in probs:
+        P1.run(-1.0, ITERS, "device")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["one_by_one_ms"] = e0.elapsed_time(e1)
+    out["one_by_one_wall_ms"] = (time.perf_counter() - t0) * 1e3
+    out["batch_speedup"] = out["one_by_one_ms"] / ms
+    for P1 in probs:
+        P1.free()
+    for A1 in mats:
+        grb.grb_free(A1)
+    grb.grb_free(ctx)
+    return out
+
+
 def run_serve_leg(grb):
     """Serving: R-MAT scale 24 resident on the device, Poisson query streams
     (seed 4) with 1-64 log-uniform seeds, FP32 ranks with FP64 residual to an
@@ -298,6 +363,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision Erdos-Renyi 2^24 leg")
     ap.add_argument("--no-ppr", action="store_true", help="skip the batched personalised PageRank leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batch leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="profiling run: only the fused device loop, on --scale/--iters (no JSON contract)")
     ap.add_argument("--scale", type=int, default=SCALE)
@@ -465,6 +531,7 @@ def main():
     mixed_leg = run_mixed_leg(grb, torch, stream) if not args.no_mixed else None
     ppr_leg = run_ppr_leg(grb, torch, stream) if not args.no_ppr else None
     serve_leg = run_serve_leg(grb) if not args.no_serve else None
+    batch_leg = run_batch_leg(grb, torch, stream) if not args.no_batch else None
 
     # ---------------------------------------------------------- roofline
     # algorithmic bytes of one launch of the persistent kernel: per body
@@ -507,6 +574,7 @@ def main():
         "mixed_er24": mixed_leg,
         "batched_ppr_rmat20_k64": ppr_leg,
         "serving_rmat24": serve_leg,
+        "graph_batch_512": batch_leg,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and not args.no_oracle:
