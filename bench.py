@@ -78,6 +78,27 @@ def _clocks_summary(path, device_index):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons)}
 
 
+def _max_over_ranks(x: float) -> float:
+    """Max of x over the ranks of the process group (x itself without one).
+    The bench's step time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_gteps(world_size: int, m: int, iters: int, ms: float) -> float:
+    """Whole-job throughput: every rank solves its own replica of the graph
+    (weak scaling), so the job does world_size * m * iters edge updates in
+    the slowest rank's time."""
+    return world_size * m * iters / (ms * 1e-3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -118,6 +139,80 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def run_profile_case_ppr(args):
+    """Profiling run of the batched personalised PageRank: R-MAT --scale,
+    --slots queries (1-32 seeds, seed 3), --iters bodies per run."""
+    import torch
+
+    import graphgen
+    import paper_2509_14211_gb300 as grb
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    torch.cuda.set_device(0)
+    n = 1 << args.scale
+    src, dst = graphgen.rmat_edges(args.scale, EDGE_FACTOR, seed=3)
+    sets = graphgen.ppr_seed_sets(n, args.slots, 1, 32, seed=3)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    m = grb.grb_matrix_nvals(AT)
+    P = grb.grb_ppr_new(AT, DAMPING, args.slots)
+    ms = 0.0
+    for rep in range(args.warmup + args.steps):
+        for s, S in enumerate(sets):
+            grb.grb_ppr_set(P, s, S, -1.0, args.iters)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        grb.grb_ppr_run(P, args.iters)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            ms += e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"profile_case": "ppr", "scale": args.scale, "n": n, "m": m, "slots": args.slots,
+                      "bodies": args.iters, "ms": ms, "ms_per_body": ms / args.iters,
+                      "edge_query_updates_per_s_G": m * args.slots * args.iters / (ms * 1e-3) / 1e9}), flush=True)
+    grb.grb_free(P)
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
+
+
+def run_profile_case_batch(args):
+    """Profiling run of the 512-graph batch (scale 8-16, edge factor 8-32,
+    seed 3): --iters bodies per run."""
+    import torch
+
+    import graphgen
+    import paper_2509_14211_gb300 as grb
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    torch.cuda.set_device(0)
+    graphs = []
+    for scale, ef, s in graphgen.batch_graph_specs(512, 8, 16, 8, 32, seed=3):
+        src, dst = graphgen.rmat_edges(scale, ef, seed=s)
+        graphs.append((1 << scale, src, dst))
+    n, src, dst, vptr = grb.block_diagonal_edges(graphs)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    m = grb.grb_matrix_nvals(AT)
+    B = grb.grb_prbatch_new(AT, vptr, DAMPING)
+    _, chosen = grb.grb_prbatch_tune(B, 2)
+    ms = 0.0
+    for rep in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        grb.grb_prbatch_run(B, -1.0, args.iters, args.iters)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            ms += e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"profile_case": "batch", "graphs": len(graphs), "n": n, "m": m, "bodies": args.iters,
+                      "chosen_ctas_per_sm": chosen, "ms": ms,
+                      "gteps": m * args.iters / (ms * 1e-3) / 1e9}), flush=True)
+    grb.grb_free(B)
+    grb.grb_free(AT)
+    grb.grb_free(ctx)
 
 
 def run_profile_case(args):
@@ -374,10 +469,17 @@ def main():
     ap.add_argument("--no-relabel", action="store_true", help="profiling run on the matrix in its input vertex order")
     ap.add_argument("--hot-bytes", type=int, default=None, help="profiling run: shared-memory hot copy size")
     ap.add_argument("--graph", default="rmat", choices=["rmat", "er"], help="profiling run: graph family")
+    ap.add_argument("--case", default="pagerank", choices=["pagerank", "ppr", "batch"],
+                    help="profiling run: the device PageRank loop, batched personalised PageRank, or the graph batch")
+    ap.add_argument("--slots", type=int, default=64, help="profiling run (ppr): number of queries")
     ap.add_argument("--mixed", action="store_true", help="profiling run: BF16 gather, then FP32")
     ap.add_argument("--tol", type=float, default=-1.0, help="profiling run: stop at this L1 change")
     args = ap.parse_args()
     if args.profile_case:
+        if args.case == "ppr":
+            return run_profile_case_ppr(args)
+        if args.case == "batch":
+            return run_profile_case_batch(args)
         return run_profile_case(args)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -439,15 +541,11 @@ def main():
         sampler.wait()
     clocks = _clocks_summary(clock_path, dev)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(sum(step_ms) / len(step_ms))
     r_fused = P.rank().astype(np.float64)
     rdiff = P.residual()
     hist, _ = grb.grb_iterate_history(ctx)
-    value = ws * m * ITERS / (ms * 1e-3) / 1e9
+    value = _job_gteps(ws, m, ITERS, ms)
 
     # graph-of-kernels variant of the device loop
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 2)
@@ -524,7 +622,7 @@ def main():
         del s_dev, d_dev
         if k >= args.warmup:
             e2e_ms.append(dt * 1e3)
-    e2e_t = sum(e2e_ms) / len(e2e_ms)
+    e2e_t = _max_over_ranks(sum(e2e_ms) / len(e2e_ms))
     grb.grb_free(AT)
     grb.grb_free(ctx)
 
@@ -554,7 +652,7 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "m": m, "iterations": ITERS,
                    "timing": "CUDA events on the launching stream; inputs larger than L2 (CSR 0.29 GB)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
-        "e2e": {"value": ws * m * ITERS / (e2e_t * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": e2e_t,
+        "e2e": {"value": _job_gteps(ws, m, ITERS, e2e_t), "unit": "GTEPS", "ms_per_step": e2e_t,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "includes": "pinned COO upload, GPU CSR build, setup, 50 fused iterations, rank read-back"},
         "roofline": roofline,
