@@ -43,6 +43,31 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pr_persistent_kernel_rmat22.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2509_14211_gb300", "csrc", "kernels_pr.cu")
+
+
+def _traffic_per_launch():
+    """DRAM bytes (read + write) of one 50-body launch of the persistent
+    kernel, from the committed ncu summary (a 2-body capture scaled by the
+    bodies), or None when the kernel source has changed since the capture."""
+    import hashlib
+    import re
+
+    try:
+        with open(KERNEL_SOURCE, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        with open(PROFILE_SUMMARY) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernels_pr\.cu sha256: ([0-9a-f]{64})", text)
+    m_traffic = re.search(r"traffic per 50-body launch: (\d+) bytes", text)
+    if not m_hash or not m_traffic or m_hash.group(1) != digest:
+        return None
+    return int(m_traffic.group(1))
+
+
 def _start_clock_sampler(path):
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -642,7 +667,7 @@ def main():
     kernel_ms = sum(kernel_ns) / len(kernel_ns) / 1e6
     achieved = launch_bytes / (kernel_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_kind, "kernel": "pr_persistent_kernel<float,float>",
+                "traffic": _traffic_per_launch(), "peak_source": peak_kind, "kernel": "pr_persistent_kernel<float,float,1024,1> (degree-ordered matrix, shared-memory hot copy)",
                 "kernel_ms_per_launch": kernel_ms, "algorithmic_bytes_per_launch": launch_bytes}
 
     out = {
