@@ -183,6 +183,8 @@ def run_profile_case_ppr(args):
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     P = grb.grb_ppr_new(AT, DAMPING, args.slots)
+    if args.vw:
+        grb.grb_ppr_layout(P, args.vw)
     ms = 0.0
     for rep in range(args.warmup + args.steps):
         for s, S in enumerate(sets):
@@ -196,6 +198,7 @@ def run_profile_case_ppr(args):
         if rep >= args.warmup:
             ms += e0.elapsed_time(e1) / args.steps
     print(json.dumps({"profile_case": "ppr", "scale": args.scale, "n": n, "m": m, "slots": args.slots,
+                      "vector_width": args.vw or 1,
                       "bodies": args.iters, "ms": ms, "ms_per_body": ms / args.iters,
                       "edge_query_updates_per_s_G": m * args.slots * args.iters / (ms * 1e-3) / 1e9}), flush=True)
     grb.grb_free(P)
@@ -351,6 +354,7 @@ def run_ppr_leg(grb, torch, stream):
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     P = grb.grb_ppr_new(AT, DAMPING, k)
+    tune_ms, vw = grb.grb_ppr_tune(P, 2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
     for rep in range(4):
@@ -367,6 +371,8 @@ def run_ppr_leg(grb, torch, stream):
     out = {"workload": "R-MAT scale 20 (1,048,576 vertices, edge factor 16, seed 3), 64 personalised queries with "
                        "1-32 uniform seeds each, FP32, 50 bodies, uniform dangling",
            "n": n, "m": m, "k": k, "bodies": iters, "ms": ms, "ms_per_body": ms / iters,
+           "autotune_ms_per_body_by_vector_width": {"1": float(tune_ms[0]), "2": float(tune_ms[1]),
+                                                    "4": float(tune_ms[2])}, "vector_width": vw,
            "edge_query_updates_per_s_G": m * k * iters / (ms * 1e-3) / 1e9,
            "algorithmic_bytes_per_body": 4 * m + 4 * (n + 1) + 4 * k * 4 * n}
     out["hbm_frac_of_measured"] = out["algorithmic_bytes_per_body"] / (out["ms_per_body"] * 1e-3) / 1e9 / _peaks()[0]
@@ -464,6 +470,7 @@ def run_serve_leg(grb):
                               mem_fraction=0.5)
         lat = r["latency_s"]
         out["levels"].append({"offered_qps": rate, "queries": count, "answered_qps": count / r["wall_s"],
+                              "vector_width": r["vector_width"],
                               "p50_ms": float(np.percentile(lat, 50) * 1e3),
                               "p99_ms": float(np.percentile(lat, 99) * 1e3),
                               "mean_bodies": float(np.mean(r["iters"])), "slots": r["slots"],
@@ -497,6 +504,7 @@ def main():
     ap.add_argument("--case", default="pagerank", choices=["pagerank", "ppr", "batch"],
                     help="profiling run: the device PageRank loop, batched personalised PageRank, or the graph batch")
     ap.add_argument("--slots", type=int, default=64, help="profiling run (ppr): number of queries")
+    ap.add_argument("--vw", type=int, default=0, help="profiling run (ppr): slots per lane (0: 1)")
     ap.add_argument("--mixed", action="store_true", help="profiling run: BF16 gather, then FP32")
     ap.add_argument("--tol", type=float, default=-1.0, help="profiling run: stop at this L1 change")
     args = ap.parse_args()

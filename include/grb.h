@@ -318,12 +318,24 @@ typedef struct grb_ppr_s* grb_ppr;
 #define GRB_PPR_MAX_SLOTS 128
 
 /* New batch object with `slots` slots (rounded up to a multiple of 32;
- * grb_ppr_slots returns the count), all empty.  Device memory: about
+ * grb_ppr_slots returns the count), all empty, vector width 1.  Device memory: about
  * 16 * n * slots bytes.  Errors: GRB_NULL_POINTER, GRB_UNINITIALIZED_OBJECT,
  * GRB_INVALID_VALUE (non-square or valued matrix, slots outside
  * 1..GRB_PPR_MAX_SLOTS, damping outside [0, 1)), GRB_OUT_OF_MEMORY. */
 grb_info grb_ppr_new(grb_ppr* P, grb_matrix AT, double damping, int32_t slots);
 grb_info grb_ppr_slots(grb_ppr P, int32_t* slots);
+
+/* Autotuner: each lane of a warp carries V = 1, 2 or 4 consecutive slots
+ * (vector width; a k-tile holds 32 V slots).  Times trial_bodies (1..100)
+ * bodies of every width with all slots busy and keeps the fastest;
+ * ms_per_body[3] (optional) gets the times for V = 1, 2, 4, *chosen_vw
+ * (optional) the winner.  Empties every slot; the slot count may grow to
+ * a multiple of 32 V (grb_ppr_slots). */
+grb_info grb_ppr_tune(grb_ppr P, int64_t trial_bodies, double* ms_per_body, int32_t* chosen_vw);
+
+/* Set the vector width (1, 2 or 4) directly; empties every slot.  Results do
+ * not depend on the width. */
+grb_info grb_ppr_layout(grb_ppr P, int32_t vw);
 
 /* Start a query in `slot` (replacing whatever it held): seeds are host
  * vertex ids (nseeds >= 1; copied), tol and itermax its loop test.
@@ -355,8 +367,9 @@ grb_info grb_ppr_get(grb_ppr P, int32_t slot, float* ranks, int out_is_device);
  * in flight, retires the finished ones and repeats, sleeping while idle.
  * Slots: as many as mem_fraction of the free device memory holds (about
  * 16 n bytes each), at most `slots` when slots > 0 and GRB_PPR_MAX_SLOTS;
- * more arrivals than slots wait in arrival order.  A query's result is the
- * one it gets alone (grb_ppr).  Returns when every query is answered. */
+ * more arrivals than slots wait in arrival order.  The vector width is picked
+ * by grb_ppr_tune before the first arrival.  A query's result is the one it
+ * gets alone (grb_ppr).  Returns when every query is answered. */
 typedef struct grb_serve_config {
     double damping;
     double tol;            /* each query's loop test: rdiff > tol */
@@ -372,6 +385,7 @@ typedef struct grb_serve_result {
     double* resid;         /* [nq] final rdiff */
     float* ranks;          /* [nq * n] host ranks, or NULL to skip */
     int32_t slots;         /* out: slots used */
+    int32_t vector_width;  /* out: slots per lane the autotuner chose */
     int64_t steps;         /* out: scheduling steps (graph launches) */
     int64_t max_in_flight; /* out */
     double wall_s;         /* out: time from start to the last answer */

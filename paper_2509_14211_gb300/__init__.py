@@ -72,7 +72,8 @@ class grb_serve_config(ctypes.Structure):
 
 class grb_serve_result(ctypes.Structure):
     _fields_ = [("latency_s", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("resid", ctypes.c_void_p),
-                ("ranks", ctypes.c_void_p), ("slots", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("ranks", ctypes.c_void_p), ("slots", ctypes.c_int32), ("vector_width", ctypes.c_int32),
+                ("steps", ctypes.c_int64),
                 ("max_in_flight", ctypes.c_int64), ("wall_s", ctypes.c_double)]
 
 
@@ -132,6 +133,8 @@ def _declare(lib):
         "grb_reduce_dense_noalloc": [V, I, U64, I, V, V],
         "grb_ppr_new": [P(V), V, D, ctypes.c_int32],
         "grb_ppr_slots": [V, P(ctypes.c_int32)],
+        "grb_ppr_tune": [V, I64, V, V],
+        "grb_ppr_layout": [V, ctypes.c_int32],
         "grb_ppr_set": [V, ctypes.c_int32, V, I64, D, I64],
         "grb_ppr_clear": [V, ctypes.c_int32],
         "grb_ppr_run": [V, I64],
@@ -174,7 +177,8 @@ def symbols():
                         "grb_apply", "grb_apply_bind2nd", "grb_apply_bind2nd_scalar", "grb_assign_scalar",
                         "grb_mxv", "grb_ewise_add", "grb_ewise_mult", "grb_reduce", "grb_wait",
                         "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
-                        "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc", "grb_ppr_new", "grb_ppr_slots",
+                        "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc", "grb_ppr_new", "grb_ppr_slots", "grb_ppr_tune",
+                        "grb_ppr_layout",
                         "grb_ppr_set", "grb_ppr_clear", "grb_ppr_run", "grb_ppr_status", "grb_ppr_get",
                         "grb_ppr_serve", "grb_prbatch_new", "grb_prbatch_tune", "grb_prbatch_run",
                         "grb_prbatch_result")
@@ -443,6 +447,18 @@ def grb_ppr_slots(P: int) -> int:
     return k.value
 
 
+def grb_ppr_tune(P: int, trial_bodies: int = 2):
+    """(ms per body for vector widths 1, 2, 4; chosen width).  Empties every slot."""
+    ms = np.zeros(3, np.float64)
+    vw = ctypes.c_int32()
+    _check(load().grb_ppr_tune(P, int(trial_bodies), ms.ctypes.data, ctypes.byref(vw)), "grb_ppr_tune")
+    return ms, vw.value
+
+
+def grb_ppr_layout(P: int, vw: int) -> None:
+    _check(load().grb_ppr_layout(P, int(vw)), "grb_ppr_layout")
+
+
 def grb_ppr_set(P: int, slot: int, seeds, tol: float, itermax: int) -> None:
     seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     _check(load().grb_ppr_set(P, int(slot), seeds.ctypes.data, len(seeds), float(tol), int(itermax)), "grb_ppr_set")
@@ -499,10 +515,11 @@ def grb_ppr_serve(AT: int, arrival_s, seed_sets, damping: float = 0.85, tol: flo
         ranks = np.zeros((nq, n), np.float32)
     cfg = grb_serve_config(float(damping), float(tol), int(itermax), int(chunk), int(slots), float(mem_fraction))
     out = grb_serve_result(lat.ctypes.data, its.ctypes.data, res.ctypes.data,
-                           ranks.ctypes.data if ranks is not None else None, 0, 0, 0, 0.0)
+                           ranks.ctypes.data if ranks is not None else None, 0, 0, 0, 0, 0.0)
     _check(load().grb_ppr_serve(AT, ctypes.byref(cfg), nq, arrival.ctypes.data, ptr.ctypes.data, idx.ctypes.data,
                                 ctypes.byref(out)), "grb_ppr_serve", AT)
-    return {"latency_s": lat, "iters": its, "resid": res, "ranks": ranks, "slots": out.slots, "steps": out.steps,
+    return {"latency_s": lat, "iters": its, "resid": res, "ranks": ranks, "slots": out.slots,
+            "vector_width": out.vector_width, "steps": out.steps,
             "max_in_flight": out.max_in_flight, "wall_s": out.wall_s}
 
 

@@ -301,8 +301,9 @@ cudaError_t launch_permute_bits(cudaStream_t st, int32_t n, const int32_t* new2o
                                 uint32_t* out_bits);
 // ------------------------------------------------ batched personalised PageRank
 // k queries ("slots") iterate together over one A^T: ranks are stored as
-// [k-tile][n][PPR_LANES] FP32, so one slot is one lane of a warp and the
-// gather of a source vertex's values for a k-tile is one 128-byte line.
+// [k-tile][n][32 V] FP32 -- lane l of a warp owns the V consecutive slots
+// l V .. l V + V - 1 of a k-tile (V = 1, 2 or 4, the vector width) -- so the
+// gather of a source vertex's values for a k-tile is 128 V contiguous bytes.
 constexpr int PPR_LANES = 32;
 constexpr int PPR_BLOCK = 512;
 constexpr int PPR_MAX_SLOTS = GRB_PPR_MAX_SLOTS;   // 4 k-tiles
@@ -318,21 +319,22 @@ struct PprParams {
     const int32_t* empty_rows = nullptr;
     int32_t n_empty = 0;
     const FixDesc* fix = nullptr;
-    // ranks and gather values, [kt][n][32]
+    // ranks and gather values, [kt][n][32 vw]
     int32_t kt = 0;
+    int32_t vw = 1;                     // slots per lane
     const float* r_old = nullptr;
     float* r_new = nullptr;
     const float* w_old = nullptr;
     float* w_new = nullptr;
     const float* dd = nullptr;          // n: max(outdeg, 1) / damping
     const uint32_t* sinkbits = nullptr; // n bits: no out-edges
-    float* agg = nullptr;               // [kt][ntiles][32] carry of the row open at a tile's end
-    float* first = nullptr;             // [kt][ntiles][32] a tile's part of its split first row
+    float* agg = nullptr;               // [kt][ntiles][32 vw] carry of the row open at a tile's end
+    float* first = nullptr;             // [kt][ntiles][32 vw] a tile's part of its split first row
     // teleport (1 - damping) v_s: seeds sorted by (k-tile, row, lane)
     const uint32_t* seedbits = nullptr; // n bits: a seed of some slot
     const int32_t* seed_ptr = nullptr;  // kt + 1 offsets
     const int32_t* seed_row = nullptr;
-    const int32_t* seed_lane = nullptr;
+    const int32_t* seed_lane = nullptr;  // slot within the k-tile
     const float* seed_val = nullptr;
     // slot state
     const int32_t* active = nullptr;    // kt*32
@@ -358,6 +360,7 @@ struct PprFinish {
 
 struct PprInit {
     int32_t slot = 0, nseeds = 0, nrows = 0;
+    int32_t width = PPR_LANES;          // slots per k-tile (32 vw)
     const int32_t* seeds = nullptr;     // device, deduplicated
     float r0 = 0.f;                     // 1 / nseeds
     float* r = nullptr;                 // current rank buffer [kt][n][32]
@@ -376,12 +379,12 @@ cudaError_t launch_ppr_finish(cudaStream_t st, const PprFinish& f);
 cudaError_t launch_ppr_init_slot(cudaStream_t st, const PprInit& a);
 // Bits of every seed vertex (bits cleared first; nbits words of 32).
 cudaError_t launch_ppr_seedbits(cudaStream_t st, int32_t nseeds, const int32_t* rows, uint32_t* bits, int64_t nwords);
-// out[i] = r[kt][i][lane] of one slot.
-cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32_t slot, float* out);
+// out[i] = r[kt][i][slot within the k-tile] of one slot.
+cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32_t width, int32_t slot, float* out);
 // FP32 divisor max(deg/damping, 1/damping) and sink bits from column counts.
 cudaError_t launch_ppr_divisor(cudaStream_t st, int32_t n, const int32_t* deg, double damping, float* dd,
                                uint32_t* sinkbits);
-int ppr_blocks_per_sm();
+int ppr_blocks_per_sm(int32_t vw);
 
 // One body of a batch of graphs: phase A, grid barrier, phase B over the
 // block-diagonal A^T; reads rbuf[from]/wbuf[from], writes the other pair

@@ -22,6 +22,8 @@ struct Ppr {
     Matrix* A = nullptr;
     double damping = 0.85;
     int32_t slots = 0, kt = 0;
+    int32_t vw = 1;                    // slots per lane (vector width)
+    int32_t requested = 0;             // slots asked for at creation
     int64_t n = 0;
     int grid = 0;
     int cur = 0;                       // which of r[2] / w[2] holds the current iterate
@@ -57,7 +59,8 @@ grb_info upload_seeds(Ppr* P) {
         const auto& S = P->seeds[s];
         if (S.empty()) continue;
         const float val = (float)((1.0 - P->damping) * (1.0 / (double)S.size()));
-        for (int32_t v : S) es.push_back({s / PPR_LANES, v, s % PPR_LANES, val});
+        const int32_t width = PPR_LANES * P->vw;
+        for (int32_t v : S) es.push_back({s / width, v, s % width, val});
     }
     std::sort(es.begin(), es.end(), [](const E& a, const E& b) {
         return a.kt != b.kt ? a.kt < b.kt : a.row != b.row ? a.row < b.row : a.lane < b.lane;
@@ -113,6 +116,7 @@ PprParams params(Ppr* P, int from) {
     p.n_empty = (int32_t)pl->n_empty;
     p.fix = (const FixDesc*)pl->fix.p;
     p.kt = P->kt;
+    p.vw = P->vw;
     p.r_old = (const float*)P->r[from].p;
     p.r_new = (float*)P->r[from ^ 1].p;
     p.w_old = (const float*)P->w[from].p;
@@ -132,7 +136,7 @@ PprParams params(Ppr* P, int from) {
 }
 
 grb_info record_iterations(Ppr* P, cudaStream_t st, int64_t iters) {
-    const int S = P->kt * PPR_LANES;
+    const int S = P->slots;
     PprFinish f;
     f.slots = S;
     f.grid_a = P->grid;
@@ -161,6 +165,51 @@ grb_info record_iterations(Ppr* P, cudaStream_t st, int64_t iters) {
         if (e == cudaSuccess) e = launch_ppr_finish(st, f);
     }
     return cuda_check(P->c, e, "ppr iteration");
+}
+
+// (Re)lay out the slot state for vector width vw: rank / gather buffers,
+// carries, partials and slot arrays, all zero; every slot empty.
+grb_info alloc_layout(Ppr* P, int32_t vw) {
+    Ctx* c = P->c;
+    drop_graph(P);
+    cudaStreamSynchronize(c->stream);
+    for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->agg, &P->first, &P->part_a, &P->part_b,
+                      &P->active, &P->iters, &P->itermax, &P->tol, &P->resid, &P->tele, &P->final_buf})
+        buf_free(c, *b);
+    const int32_t width = PPR_LANES * vw;
+    P->vw = vw;
+    P->kt = (P->requested + width - 1) / width;
+    P->slots = P->kt * width;
+    P->seeds.assign(P->slots, {});
+    P->cur = 0;
+    P->dirty = true;
+    P->grid = ppr_blocks_per_sm(vw) * c->sm_count;
+    const int64_t n = P->n, S = P->slots, nt = P->A->plan->ntiles;
+    const size_t rb = sizeof(float) * (size_t)S * (size_t)n;
+    for (int q = 0; q < 2; ++q) {
+        P->r[q] = buf_alloc(c, rb);
+        P->w[q] = buf_alloc(c, rb);
+    }
+    P->agg = buf_alloc(c, sizeof(float) * (size_t)S * nt);
+    P->first = buf_alloc(c, sizeof(float) * (size_t)S * nt);
+    P->part_a = buf_alloc(c, sizeof(double) * 2 * (size_t)P->grid * S);
+    P->part_b = buf_alloc(c, sizeof(double) * 2 * (size_t)P->grid * S);
+    P->active = buf_alloc(c, sizeof(int32_t) * S);
+    P->iters = buf_alloc(c, sizeof(int32_t) * S);
+    P->itermax = buf_alloc(c, sizeof(int32_t) * S);
+    P->tol = buf_alloc(c, sizeof(double) * S);
+    P->resid = buf_alloc(c, sizeof(double) * S);
+    P->tele = buf_alloc(c, sizeof(float) * S);
+    P->final_buf = buf_alloc(c, sizeof(int32_t) * S);
+    grb_info st = GRB_SUCCESS;
+    for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->agg, &P->first, &P->part_a, &P->part_b,
+                      &P->active, &P->iters, &P->itermax, &P->tol, &P->resid, &P->tele, &P->final_buf})
+        if (!b->p) st = GRB_OUT_OF_MEMORY;
+    for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->active, &P->iters, &P->itermax, &P->tol,
+                      &P->resid, &P->tele, &P->final_buf})
+        if (!st) st = cuda_check(c, cudaMemsetAsync(b->p, 0, b->bytes, c->stream), "ppr layout");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr layout");
+    return st;
 }
 
 }  // namespace
@@ -200,42 +249,16 @@ grb_info grb_ppr_new(grb_ppr* out, grb_matrix Am, double damping, int32_t slots)
     P->A = A;
     A->refs++;
     P->damping = damping;
-    P->kt = (slots + PPR_LANES - 1) / PPR_LANES;
-    P->slots = P->kt * PPR_LANES;
     P->n = A->nrows;
-    P->seeds.assign(P->slots, {});
-    P->grid = ppr_blocks_per_sm() * c->sm_count;
-    const int64_t n = P->n, S = P->slots, nt = A->plan->ntiles;
-    const size_t rb = sizeof(float) * (size_t)P->kt * (size_t)n * PPR_LANES;
-    for (int q = 0; q < 2; ++q) {
-        P->r[q] = buf_alloc(c, rb);
-        P->w[q] = buf_alloc(c, rb);
-    }
+    P->requested = slots;
+    const int64_t n = P->n;
     P->dd = buf_alloc(c, sizeof(float) * n);
     P->sinkbits = buf_alloc(c, sizeof(uint32_t) * ((n + 31) / 32));
     P->seedbits = buf_alloc(c, sizeof(uint32_t) * ((n + 31) / 32));
-    P->agg = buf_alloc(c, sizeof(float) * (size_t)P->kt * nt * PPR_LANES);
-    P->first = buf_alloc(c, sizeof(float) * (size_t)P->kt * nt * PPR_LANES);
-    P->part_a = buf_alloc(c, sizeof(double) * 2 * (size_t)P->grid * S);
-    P->part_b = buf_alloc(c, sizeof(double) * 2 * (size_t)P->grid * S);
-    P->active = buf_alloc(c, sizeof(int32_t) * S);
-    P->iters = buf_alloc(c, sizeof(int32_t) * S);
-    P->itermax = buf_alloc(c, sizeof(int32_t) * S);
-    P->tol = buf_alloc(c, sizeof(double) * S);
-    P->resid = buf_alloc(c, sizeof(double) * S);
-    P->tele = buf_alloc(c, sizeof(float) * S);
-    P->final_buf = buf_alloc(c, sizeof(int32_t) * S);
+    if (!P->dd.p || !P->sinkbits.p || !P->seedbits.p) st = GRB_OUT_OF_MEMORY;
+    if (!st) st = alloc_layout(P, 1);
     DevBuf deg = buf_alloc(c, sizeof(int32_t) * n), pres = buf_alloc(c, (size_t)n);
-    for (DevBuf* b : {&P->r[0], &P->r[1], &P->w[0], &P->w[1], &P->dd, &P->sinkbits, &P->seedbits, &P->agg,
-                      &P->first, &P->part_a, &P->part_b, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid,
-                      &P->tele, &P->final_buf, &deg, &pres})
-        if (!b->p) st = GRB_OUT_OF_MEMORY;
-    for (int q = 0; q < 2 && !st; ++q) {
-        st = cuda_check(c, cudaMemsetAsync(P->r[q].p, 0, rb, c->stream), "ppr init");
-        if (!st) st = cuda_check(c, cudaMemsetAsync(P->w[q].p, 0, rb, c->stream), "ppr init");
-    }
-    for (DevBuf* b : {&P->seedbits, &P->active, &P->iters, &P->itermax, &P->tol, &P->resid, &P->tele, &P->final_buf})
-        if (!st) st = cuda_check(c, cudaMemsetAsync(b->p, 0, b->bytes, c->stream), "ppr init");
+    if (!deg.p || !pres.p) st = GRB_OUT_OF_MEMORY;
     if (!st) {
         c->stats.kernel_launches += 3;
         st = cuda_check(c, launch_col_degree(c->stream, n, A->nnz, (const int32_t*)A->col_idx.p, (int32_t*)deg.p,
@@ -253,6 +276,57 @@ grb_info grb_ppr_new(grb_ppr* out, grb_matrix Am, double damping, int32_t slots)
     }
     *out = reinterpret_cast<grb_ppr>(P);
     return GRB_SUCCESS;
+}
+
+grb_info grb_ppr_layout(grb_ppr Ph, int32_t vw) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (vw != 1 && vw != 2 && vw != 4) return GRB_INVALID_VALUE;
+    return alloc_layout(P, vw);
+}
+
+grb_info grb_ppr_tune(grb_ppr Ph, int64_t trial_bodies, double* ms_per_body, int32_t* chosen_vw) {
+    Ppr* P = as_ppr(Ph);
+    if (!Ph) return GRB_NULL_POINTER;
+    if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (trial_bodies < 1 || trial_bodies > 100) return GRB_INVALID_VALUE;
+    Ctx* c = P->c;
+    const int32_t cands[3] = {1, 2, 4};
+    double best = 1e300;
+    int32_t best_vw = 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    grb_info st = cuda_check(c, cudaEventCreate(&e0), "ppr tune");
+    if (!st) st = cuda_check(c, cudaEventCreate(&e1), "ppr tune");
+    for (int q = 0; q < 3 && !st; ++q) {
+        st = alloc_layout(P, cands[q]);
+        // every slot busy with a one-vertex query
+        for (int32_t s = 0; s < P->slots && !st; ++s) {
+            const int32_t v = (int32_t)(((int64_t)s * 7919) % P->n);
+            st = grb_ppr_set(Ph, s, &v, 1, -1.0, INT32_MAX);
+        }
+        if (!st) st = grb_ppr_run(Ph, trial_bodies);   // captures the graph, warms up
+        if (!st) st = cuda_check(c, cudaEventRecord(e0, c->stream), "ppr tune");
+        if (!st) st = grb_ppr_run(Ph, trial_bodies);
+        if (!st) st = cuda_check(c, cudaEventRecord(e1, c->stream), "ppr tune");
+        if (!st) st = cuda_check(c, cudaEventSynchronize(e1), "ppr tune");
+        float ms = 0.f;
+        if (!st) st = cuda_check(c, cudaEventElapsedTime(&ms, e0, e1), "ppr tune");
+        if (st) break;
+        // time per body for the requested slots (a wider layout may round
+        // the slot count up; the extra slots do not count)
+        const double per = (double)ms / (double)trial_bodies;
+        if (ms_per_body) ms_per_body[q] = per;
+        if (per < best) {
+            best = per;
+            best_vw = cands[q];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!st) st = alloc_layout(P, best_vw);
+    if (!st && chosen_vw) *chosen_vw = best_vw;
+    return st;
 }
 
 grb_info grb_ppr_slots(grb_ppr Ph, int32_t* slots) {
@@ -280,6 +354,7 @@ grb_info grb_ppr_set(grb_ppr Ph, int32_t slot, const int32_t* seeds, int64_t nse
                                                 c->stream), "seeds");
     PprInit a;
     a.slot = slot;
+    a.width = PPR_LANES * P->vw;
     a.nseeds = (int32_t)S.size();
     a.nrows = (int32_t)P->n;
     a.seeds = (const int32_t*)ds.p;
@@ -411,7 +486,7 @@ grb_info grb_ppr_get(grb_ppr Ph, int32_t slot, float* ranks, int out_is_device) 
     const int buf = act ? P->cur : (fb & 1);
     c->stats.kernel_launches++;
     if (!st)
-        st = cuda_check(c, launch_ppr_extract(c->stream, (int32_t)P->n, (const float*)P->r[buf].p, slot, dst),
+        st = cuda_check(c, launch_ppr_extract(c->stream, (int32_t)P->n, (const float*)P->r[buf].p, PPR_LANES * P->vw, slot, dst),
                         "ppr extract");
     if (!st && !out_is_device)
         st = cuda_check(c, cudaMemcpyAsync(ranks, tmp.p, sizeof(float) * P->n, cudaMemcpyDeviceToHost, c->stream),

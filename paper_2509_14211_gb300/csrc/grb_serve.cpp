@@ -61,6 +61,13 @@ grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, c
     grb_ppr P = nullptr;
     grb_info st = grb_ppr_new(&P, AT, cfg->damping, (int32_t)cap);
     if (st) return st;
+    // vector width by the autotuner, before the clock starts
+    st = grb_ppr_tune(P, 2, nullptr, &out->vector_width);
+    if (st) {
+        void* pp = P;
+        grb_free(&pp);
+        return st;
+    }
     const int32_t S = (int32_t)std::min<int64_t>(cap, GRB_PPR_MAX_SLOTS);
     out->slots = S;
     std::vector<int32_t> slot_q(S, -1), free_slots, active(GRB_PPR_MAX_SLOTS);

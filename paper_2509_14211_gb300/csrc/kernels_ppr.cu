@@ -1,8 +1,8 @@
 // Batched personalised PageRank: k queries iterate together as one sparse x
 // dense product over A^T.  The paper's method runs one rank vector; here the
 // same fused body (division folded into the previous epilogue, row sums,
-// teleport, residual and dangling mass in the row epilogue) runs for
-// PPR_LANES slots per warp:
+// teleport, residual and dangling mass in the row epilogue) runs for many
+// slots at once:
 //
 //   r_s' = (1 - d) v_s + d D_s / n + A^T w_s,   w_s = r_s ./ dvec,
 //   D_s  = sum of r_s over vertices without out-edges,  res_s = |r_s - r_s'|_1
@@ -10,21 +10,23 @@
 // with v_s uniform over slot s's seed set (dangling mass spread over all n
 // vertices, so r_s is linear in v_s).
 //
-// Layout: r and w are [k-tile][n][32] FP32 -- lane l of a warp owns slot
-// 32*kt + l, and the values of one source vertex for a k-tile are one
-// contiguous 128-byte line, so every gather is a fully used cache line.
-// A warp walks the nonzeros of a 256-nonzero tile (the same tile plan as the
-// single-vector kernels) one by one, all lanes adding their slot's value;
-// row ends come from the row-end bitmap.  Rows split across tiles are
-// finished by ppr_fixups_kernel from per-tile carries, and
-// ppr_finish_kernel folds the per-CTA partials of every slot in a fixed
-// order.  The three kernels of an iteration are separated by kernel
-// boundaries (the caller captures iterations in a CUDA graph), so there are
-// no device-side waits.
+// Layout: r and w are [k-tile][n][32 V] FP32 -- lane l of a warp owns the V
+// consecutive slots l V .. l V + V - 1 of its k-tile (V = 1, 2, 4: the vector
+// width), and the values of one source vertex for a k-tile are 128 V
+// contiguous bytes, so every gather is fully used cache lines and one warp
+// instruction moves V slots per lane.  A warp walks the nonzeros of a
+// 256-nonzero tile (the same tile plan as the single-vector kernels) one by
+// one, all lanes adding their slots' values; row ends come from the row-end
+// bitmap.  Rows split across tiles are finished by ppr_fixups_kernel from
+// per-tile carries, and ppr_finish_kernel folds the per-CTA partials of every
+// slot in a fixed order.  The three kernels of an iteration are separated by
+// kernel boundaries (the caller captures iterations in a CUDA graph), so
+// there are no device-side waits.
 //
 // Every slot's arithmetic (row sums in tile order, carries in tile order,
 // fixed-order folds over a grid that does not depend on k) is independent of
-// the other slots: a query gives the same bits alone and in any batch.
+// the other slots and of its position: a query gives the same bits alone and
+// in any batch.
 #include "grb_device.cuh"
 
 namespace grb {
@@ -33,7 +35,6 @@ namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int NW = PPR_BLOCK / 32;
-constexpr int KT_MAX = PPR_MAX_SLOTS / PPR_LANES;
 
 struct Kahan {
     float s = 0.f, c = 0.f;
@@ -46,18 +47,74 @@ struct Kahan {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// per-warp partials of every slot: [warp][slot]
 struct PprSmem {
-    double res[KT_MAX][NW][32];
-    double dang[KT_MAX][NW][32];
+    double res[NW][PPR_MAX_SLOTS];
+    double dang[NW][PPR_MAX_SLOTS];
+};
+
+template <int V>
+struct Vec;
+template <>
+struct Vec<1> {
+    float x[1];
+    __device__ __forceinline__ void ld(const float* p) { x[0] = __ldg(p); }
+    __device__ __forceinline__ void ld_cs(const float* p) { x[0] = __ldcs(p); }
+    __device__ __forceinline__ void ld_cg(const float* p) { x[0] = __ldcg(p); }
+    __device__ __forceinline__ void st(float* p) const { *p = x[0]; }
+    __device__ __forceinline__ void st_cs(float* p) const { __stcs(p, x[0]); }
+};
+template <>
+struct Vec<2> {
+    float x[2];
+    __device__ __forceinline__ void set(float2 a) { x[0] = a.x; x[1] = a.y; }
+    __device__ __forceinline__ void ld(const float* p) { set(__ldg(reinterpret_cast<const float2*>(p))); }
+    __device__ __forceinline__ void ld_cs(const float* p) { set(__ldcs(reinterpret_cast<const float2*>(p))); }
+    __device__ __forceinline__ void ld_cg(const float* p) { set(__ldcg(reinterpret_cast<const float2*>(p))); }
+    __device__ __forceinline__ void st(float* p) const { *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]); }
+    __device__ __forceinline__ void st_cs(float* p) const {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(x[0], x[1]));
+    }
+};
+template <>
+struct Vec<4> {
+    float x[4];
+    __device__ __forceinline__ void set(float4 a) {
+        x[0] = a.x;
+        x[1] = a.y;
+        x[2] = a.z;
+        x[3] = a.w;
+    }
+    __device__ __forceinline__ void ld(const float* p) { set(__ldg(reinterpret_cast<const float4*>(p))); }
+    __device__ __forceinline__ void ld_cs(const float* p) { set(__ldcs(reinterpret_cast<const float4*>(p))); }
+    __device__ __forceinline__ void ld_cg(const float* p) { set(__ldcg(reinterpret_cast<const float4*>(p))); }
+    __device__ __forceinline__ void st(float* p) const {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+    __device__ __forceinline__ void st_cs(float* p) const {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
+    }
+};
+
+// Per-lane state of the lane's V slots in the current k-tile.
+template <int V>
+struct Lane {
+    bool act[V];
+    float tb[V];
+    Kahan res[V], dang[V];
+    bool any;
 };
 
 __device__ __forceinline__ bool bit_of(const uint32_t* b, int i) { return (__ldg(b + (i >> 5)) >> (i & 31)) & 1u; }
 
-// (1 - d) v_s[i] for this lane's slot.  The seed bitmap filters almost every
-// row; on a hit the k-tile's seed rows (sorted) are binary-searched.  The row
-// is the same for the whole warp, so the control flow is uniform.
-__device__ __forceinline__ float seed_term(const PprParams& p, int kt, int i, int lane) {
-    if (!bit_of(p.seedbits, i)) return 0.f;
+// (1 - d) v_s[i] for this lane's slots.  The seed bitmap filters almost
+// every row; on a hit the k-tile's seed rows (sorted) are binary-searched.
+// The row is the same for the whole warp, so the control flow is uniform.
+template <int V>
+__device__ __forceinline__ void seed_terms(const PprParams& p, int kt, int i, int lane, float (&sv)[V]) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) sv[v] = 0.f;
+    if (!bit_of(p.seedbits, i)) return;
     int lo = __ldg(p.seed_ptr + kt), hi = __ldg(p.seed_ptr + kt + 1);
     const int end = hi;
     while (lo < hi) {
@@ -65,60 +122,111 @@ __device__ __forceinline__ float seed_term(const PprParams& p, int kt, int i, in
         if (__ldg(p.seed_row + mid) < i) lo = mid + 1;
         else hi = mid;
     }
-    float v = 0.f;
-    for (int e = lo; e < end && __ldg(p.seed_row + e) == i; ++e)
-        if (__ldg(p.seed_lane + e) == lane) v = __ldg(p.seed_val + e);
-    return v;
+    for (int e = lo; e < end && __ldg(p.seed_row + e) == i; ++e) {
+        const int s = __ldg(p.seed_lane + e);   // slot within the k-tile
+        if (s / V == lane) {
+            const float val = __ldg(p.seed_val + e);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (s % V == v) sv[v] = val;
+        }
+    }
 }
 
-// Epilogue of row i for this lane's slot: r' = (seed + d D / n) + sum, the
+// Epilogue of row i for this lane's slots: r' = (seed + d D / n) + sum, the
 // next gather value, and the residual / dangling-mass terms.  A finished
 // (inactive) slot writes nothing: its last iterate stays in the buffer the
 // finish kernel recorded.
-__device__ __forceinline__ void ppr_row(const PprParams& p, int kt, int i, float sum, int lane, bool act, float tb,
-                                        Kahan& res, Kahan& dang) {
-    const float sv = seed_term(p, kt, i, lane);   // uniform across the warp
-    if (!act) return;
-    const size_t o = ((size_t)kt * (size_t)p.nrows + (size_t)i) * PPR_LANES + (size_t)lane;
-    const float rold = __ldcs(p.r_old + o);
+template <int V>
+__device__ __forceinline__ void ppr_row(const PprParams& p, int kt, int i, const float (&sum)[V], int lane,
+                                        Lane<V>& L) {
+    float sv[V];
+    seed_terms<V>(p, kt, i, lane, sv);   // uniform across the warp
+    if (!L.any) return;
+    const size_t o = ((size_t)kt * (size_t)p.nrows + (size_t)i) * (PPR_LANES * V) + (size_t)lane * V;
+    Vec<V> rold, rn, wn;
+    rold.ld_cs(p.r_old + o);
     const float dd = __ldg(p.dd + i);
-    const float rn = (sv + tb) + sum;
-    __stcs(p.r_new + o, rn);
-    p.w_new[o] = rn / dd;
-    res.add(fabsf(rold - rn));
-    if (bit_of(p.sinkbits, i)) dang.add(rn);
+    const bool sink = bit_of(p.sinkbits, i);
+    bool all = true;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        rn.x[v] = (sv[v] + L.tb[v]) + sum[v];
+        wn.x[v] = rn.x[v] / dd;
+        all = all && L.act[v];
+        if (L.act[v]) {
+            L.res[v].add(fabsf(rold.x[v] - rn.x[v]));
+            if (sink) L.dang[v].add(rn.x[v]);
+        }
+    }
+    if (all) {
+        rn.st_cs(p.r_new + o);
+        wn.st(p.w_new + o);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (L.act[v]) {
+                p.r_new[o + v] = rn.x[v];
+                p.w_new[o + v] = wn.x[v];
+            }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void lane_begin(const PprParams& p, int kt, int lane, Lane<V>& L) {
+    const int base = kt * PPR_LANES * V + lane * V;
+    L.any = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        L.act[v] = __ldg(p.active + base + v) != 0;
+        L.tb[v] = __ldg(p.tele_base + base + v);
+        L.res[v] = Kahan();
+        L.dang[v] = Kahan();
+        L.any = L.any || L.act[v];
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void lane_end(int kt, int lane, int warp, const Lane<V>& L, PprSmem& sm) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int s = kt * PPR_LANES * V + lane * V + v;
+        sm.res[warp][s] = L.res[v].value();
+        sm.dang[warp][s] = L.dang[v].value();
+    }
 }
 
 // Per-CTA partials of every slot: the warps' accumulators folded in warp
 // order.
 __device__ __forceinline__ void flush_slot_partials(const PprParams& p, PprSmem& sm) {
     __syncthreads();
-    const int S = p.kt * PPR_LANES;
+    const int S = p.kt * PPR_LANES * p.vw;
     for (int s = threadIdx.x; s < S; s += PPR_BLOCK) {
-        const int kt = s / PPR_LANES, l = s % PPR_LANES;
         double a = 0.0, b = 0.0;
         for (int w = 0; w < NW; ++w) {
-            a += sm.res[kt][w][l];
-            b += sm.dang[kt][w][l];
+            a += sm.res[w][s];
+            b += sm.dang[w][s];
         }
         p.part[((size_t)blockIdx.x * S + s) * 2] = a;
         p.part[((size_t)blockIdx.x * S + s) * 2 + 1] = b;
     }
 }
 
-__device__ __forceinline__ void zero_smem(PprSmem& sm, int kts) {
-    for (int q = threadIdx.x; q < kts * NW * 32; q += PPR_BLOCK) {
-        (&sm.res[0][0][0])[q] = 0.0;
-        (&sm.dang[0][0][0])[q] = 0.0;
+__device__ __forceinline__ void zero_smem(PprSmem& sm) {
+    for (int q = threadIdx.x; q < NW * PPR_MAX_SLOTS; q += PPR_BLOCK) {
+        (&sm.res[0][0])[q] = 0.0;
+        (&sm.dang[0][0])[q] = 0.0;
     }
     __syncthreads();
 }
 
-// Phase A: the warp tiles, k-tile by k-tile (so the warps of the GPU share
-// one k-tile of w in L2 at a time), then the empty rows.  Tile t goes to the
-// same warp in every k-tile, so every slot sees the same summation order.
-__device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int lane, bool act, float tb, Kahan& res,
-                                         Kahan& dang) {
+// Phase A for one tile: the warp walks the tile's nonzeros; the lane adds its
+// slots' values of each source vertex.  Loads are issued U nonzeros at a
+// time (U V floats per lane in flight).
+template <int V>
+__device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int lane, Lane<V>& L) {
+    constexpr int U = V == 4 ? 4 : 8;
+    constexpr int W = PPR_LANES * V;
     const uint32_t meta = __ldg(p.tile_meta + t);
     const int rfirst = (int)(meta & 0x7fffffffu);
     const int x_lo = (int)(meta >> 31);
@@ -128,9 +236,11 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
     const uint32_t myf = (__ldcs(p.rowend_bits + (kl >> 5)) >> (kl & 31)) & 0xffu;
     const int nvalid = min(max(p.nnz - t * PR_NZTILE, 0), PR_NZTILE);
     const int pre_i = rfirst + lane < p.n_ne ? __ldg(p.ne_rows + rfirst + lane) : 0;
-    const float* W = p.w_old + (size_t)kt * (size_t)p.nrows * PPR_LANES + lane;
-    const size_t tslot = ((size_t)kt * p.ntiles + t) * PPR_LANES + lane;
-    float acc = 0.f;
+    const float* Wb = p.w_old + (size_t)kt * (size_t)p.nrows * W + (size_t)lane * V;
+    const size_t tslot = ((size_t)kt * p.ntiles + t) * W + (size_t)lane * V;
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
     int r = 0;   // rows of the tile finished so far (the same in every lane)
     for (int src = 0; src < 32; ++src) {
         if (src * PR_NZLANE >= nvalid) break;
@@ -145,51 +255,70 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
         c[6] = __shfl_sync(FULL, cb.z, src);
         c[7] = __shfl_sync(FULL, cb.w, src);
         const uint32_t f = __shfl_sync(FULL, myf, src);
-        float v[PR_NZLANE];
 #pragma unroll
-        for (int q = 0; q < PR_NZLANE; ++q)
-            v[q] = src * PR_NZLANE + q < nvalid ? __ldg(W + (size_t)c[q] * PPR_LANES) : 0.f;
+        for (int q0 = 0; q0 < PR_NZLANE; q0 += U) {
+            Vec<V> g[U];
 #pragma unroll
-        for (int q = 0; q < PR_NZLANE; ++q) {
-            acc += v[q];
-            if ((f >> q) & 1u) {
-                if (r == 0 && x_lo) {
-                    p.first[tslot] = acc;   // a row begun in an earlier tile: phase B
+            for (int q = 0; q < U; ++q) {
+                if (src * PR_NZLANE + q0 + q < nvalid) {
+                    g[q].ld(Wb + (size_t)c[q0 + q] * W);
                 } else {
-                    const int i = r < 32 ? __shfl_sync(FULL, pre_i, r) : __ldg(p.ne_rows + rfirst + r);
-                    ppr_row(p, kt, i, acc, lane, act, tb, res, dang);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) g[q].x[v] = 0.f;
                 }
-                ++r;
-                acc = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += g[q].x[v];
+                if ((f >> (q0 + q)) & 1u) {
+                    if (r == 0 && x_lo) {
+                        Vec<V> a;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) a.x[v] = acc[v];
+                        a.st(p.first + tslot);   // a row begun in an earlier tile: phase B
+                    } else {
+                        const int i = r < 32 ? __shfl_sync(FULL, pre_i, r) : __ldg(p.ne_rows + rfirst + r);
+                        ppr_row<V>(p, kt, i, acc, lane, L);
+                    }
+                    ++r;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+                }
             }
         }
     }
-    p.agg[tslot] = acc;   // the row still open at the tile's end
+    Vec<V> a;
+#pragma unroll
+    for (int v = 0; v < V; ++v) a.x[v] = acc[v];
+    a.st(p.agg + tslot);   // the row still open at the tile's end
 }
 
-__global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_tiles_kernel(const __grid_constant__ PprParams p) {
+// Phase A: the warp tiles, k-tile by k-tile (so the warps of the GPU share
+// one k-tile of w in L2 at a time), then the empty rows.  Tile t goes to the
+// same warp in every k-tile, so every slot sees the same summation order.
+// The V = 4 tile loop keeps 16 gathered floats, 4 sums and 8 compensated
+// accumulators per lane: it gets the registers of one CTA per SM.
+template <int V>
+__global__ void __launch_bounds__(PPR_BLOCK, (V == 4 ? 1 : 2)) ppr_tiles_kernel(const __grid_constant__ PprParams p) {
     __shared__ PprSmem sm;
-    zero_smem(sm, p.kt);
+    zero_smem(sm);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = gridDim.x * NW;
     const int w0 = blockIdx.x * NW + warp;
     for (int kt = 0; kt < p.kt; ++kt) {
-        Kahan res, dang;
-        const bool act = __ldg(p.active + kt * PPR_LANES + lane) != 0;
-        const float tb = __ldg(p.tele_base + kt * PPR_LANES + lane);
+        Lane<V> L;
+        lane_begin<V>(p, kt, lane, L);
         // a k-tile without an active slot is skipped (the same decision in
         // every warp: all read the same flags)
-        if (!__any_sync(FULL, act)) {
-            sm.res[kt][warp][lane] = 0.0;
-            sm.dang[kt][warp][lane] = 0.0;
-            continue;
-        }
-        for (int t = w0; t < p.ntiles; t += nwarps) ppr_tile(p, kt, t, lane, act, tb, res, dang);
+        if (!__any_sync(FULL, L.any)) continue;
+        for (int t = w0; t < p.ntiles; t += nwarps) ppr_tile<V>(p, kt, t, lane, L);
         // rows without nonzeros: the epilogue with an empty sum
-        for (int e = w0; e < p.n_empty; e += nwarps)
-            ppr_row(p, kt, __ldg(p.empty_rows + e), 0.f, lane, act, tb, res, dang);
-        sm.res[kt][warp][lane] = res.value();
-        sm.dang[kt][warp][lane] = dang.value();
+        float zero[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) zero[v] = 0.f;
+        for (int e = w0; e < p.n_empty; e += nwarps) ppr_row<V>(p, kt, __ldg(p.empty_rows + e), zero, lane, L);
+        lane_end<V>(kt, lane, warp, L, sm);
     }
     flush_slot_partials(p, sm);
 }
@@ -197,31 +326,37 @@ __global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_tiles_kernel(const __grid_co
 // Phase B: rows split across tiles, one warp per (k-tile, tile) with a
 // fixup: the carries of the earlier tiles in tile order, then this tile's
 // part.
+template <int V>
 __global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_fixups_kernel(const __grid_constant__ PprParams p) {
     __shared__ PprSmem sm;
-    zero_smem(sm, p.kt);
+    zero_smem(sm);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = gridDim.x * NW;
+    constexpr int W = PPR_LANES * V;
     for (int kt = 0; kt < p.kt; ++kt) {
-        Kahan res, dang;
-        const bool act = __ldg(p.active + kt * PPR_LANES + lane) != 0;
-        const float tb = __ldg(p.tele_base + kt * PPR_LANES + lane);
-        if (!__any_sync(FULL, act)) {
-            sm.res[kt][warp][lane] = 0.0;
-            sm.dang[kt][warp][lane] = 0.0;
-            continue;
-        }
+        Lane<V> L;
+        lane_begin<V>(p, kt, lane, L);
+        if (!__any_sync(FULL, L.any)) continue;
         for (int t = blockIdx.x * NW + warp; t < p.ntiles; t += nwarps) {
             const FixDesc f = p.fix[t];
             if (f.row < 0) continue;
-            const size_t base = (size_t)kt * p.ntiles * PPR_LANES + lane;
-            float sum = 0.f;
-            for (int tt = f.ts; tt < t; ++tt) sum += __ldcg(p.agg + base + (size_t)tt * PPR_LANES);
-            sum += __ldcg(p.first + base + (size_t)t * PPR_LANES);
-            ppr_row(p, kt, f.row, sum, lane, act, tb, res, dang);
+            const size_t base = (size_t)kt * p.ntiles * W + (size_t)lane * V;
+            float sum[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) sum[v] = 0.f;
+            for (int tt = f.ts; tt < t; ++tt) {
+                Vec<V> a;
+                a.ld_cg(p.agg + base + (size_t)tt * W);
+#pragma unroll
+                for (int v = 0; v < V; ++v) sum[v] += a.x[v];
+            }
+            Vec<V> a;
+            a.ld_cg(p.first + base + (size_t)t * W);
+#pragma unroll
+            for (int v = 0; v < V; ++v) sum[v] += a.x[v];
+            ppr_row<V>(p, kt, f.row, sum, lane, L);
         }
-        sm.res[kt][warp][lane] = res.value();
-        sm.dang[kt][warp][lane] = dang.value();
+        lane_end<V>(kt, lane, warp, L, sm);
     }
     flush_slot_partials(p, sm);
 }
@@ -261,25 +396,25 @@ __global__ void ppr_finish_kernel(const __grid_constant__ PprFinish f) {
 }
 
 __global__ void ppr_init_zero_kernel(PprInit a) {
-    const int kt = a.slot / PPR_LANES, l = a.slot % PPR_LANES;
+    const int kt = a.slot / a.width, l = a.slot % a.width;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nrows; i += gridDim.x * blockDim.x) {
-        const size_t o = ((size_t)kt * a.nrows + i) * PPR_LANES + l;
+        const size_t o = ((size_t)kt * a.nrows + i) * a.width + l;
         a.r[o] = 0.f;
         a.w[o] = 0.f;
     }
 }
 
 __global__ void ppr_init_seed_kernel(PprInit a) {
-    const int kt = a.slot / PPR_LANES, l = a.slot % PPR_LANES;
-    double D = 0.0;
+    const int kt = a.slot / a.width, l = a.slot % a.width;
     for (int q = threadIdx.x; q < a.nseeds; q += blockDim.x) {
         const int i = a.seeds[q];
-        const size_t o = ((size_t)kt * a.nrows + i) * PPR_LANES + l;
+        const size_t o = ((size_t)kt * a.nrows + i) * a.width + l;
         a.r[o] = a.r0;
         a.w[o] = a.r0 / a.dd[i];
     }
     // dangling mass of the start vector (one thread, in seed order)
     if (threadIdx.x == 0) {
+        double D = 0.0;
         for (int q = 0; q < a.nseeds; ++q)
             if ((a.sinkbits[a.seeds[q] >> 5] >> (a.seeds[q] & 31)) & 1u) D += (double)a.r0;
         a.tele_base[a.slot] = (float)(a.damping * D / (double)a.nrows);
@@ -291,10 +426,10 @@ __global__ void ppr_seedbits_kernel(int32_t nseeds, const int32_t* rows, uint32_
         atomicOr(bits + (rows[q] >> 5), 1u << (rows[q] & 31));
 }
 
-__global__ void ppr_extract_kernel(int32_t n, const float* r, int32_t slot, float* out) {
-    const int kt = slot / PPR_LANES, l = slot % PPR_LANES;
+__global__ void ppr_extract_kernel(int32_t n, const float* r, int32_t width, int32_t slot, float* out) {
+    const int kt = slot / width, l = slot % width;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = r[((size_t)kt * n + i) * PPR_LANES + l];
+        out[i] = r[((size_t)kt * n + i) * width + l];
 }
 
 __global__ void ppr_divisor_kernel(int32_t n, const int32_t* deg, double damping, float* dd, uint32_t* sinkbits) {
@@ -318,26 +453,44 @@ inline int grid_1d(int64_t n, int block = 256) {
     return (int)(g < 1 ? 1 : g);
 }
 
-}  // namespace
-
-int ppr_blocks_per_sm() {
+template <class K>
+int occ(K k) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ppr_tiles_kernel, PPR_BLOCK, 0) != cudaSuccess) return 1;
-    int nb2 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, ppr_fixups_kernel, PPR_BLOCK, 0) != cudaSuccess) return 1;
-    nb = nb < nb2 ? nb : nb2;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, PPR_BLOCK, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
+bool valid_vw(int32_t vw) { return vw == 1 || vw == 2 || vw == 4; }
+
+}  // namespace
+
+int ppr_blocks_per_sm(int32_t vw) {
+    int a = 1, b = 1;
+    switch (vw) {
+        case 1: a = occ(ppr_tiles_kernel<1>); b = occ(ppr_fixups_kernel<1>); break;
+        case 2: a = occ(ppr_tiles_kernel<2>); b = occ(ppr_fixups_kernel<2>); break;
+        case 4: a = occ(ppr_tiles_kernel<4>); b = occ(ppr_fixups_kernel<4>); break;
+    }
+    return a < b ? a : b;
+}
+
 cudaError_t launch_ppr_tiles(cudaStream_t st, const PprParams& p, int grid) {
-    if (p.kt < 1 || p.kt > KT_MAX) return cudaErrorInvalidValue;
-    ppr_tiles_kernel<<<grid, PPR_BLOCK, 0, st>>>(p);
+    if (!valid_vw(p.vw) || p.kt < 1 || p.kt * PPR_LANES * p.vw > PPR_MAX_SLOTS) return cudaErrorInvalidValue;
+    switch (p.vw) {
+        case 1: ppr_tiles_kernel<1><<<grid, PPR_BLOCK, 0, st>>>(p); break;
+        case 2: ppr_tiles_kernel<2><<<grid, PPR_BLOCK, 0, st>>>(p); break;
+        default: ppr_tiles_kernel<4><<<grid, PPR_BLOCK, 0, st>>>(p); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_ppr_fixups(cudaStream_t st, const PprParams& p, int grid) {
-    if (p.kt < 1 || p.kt > KT_MAX) return cudaErrorInvalidValue;
-    ppr_fixups_kernel<<<grid, PPR_BLOCK, 0, st>>>(p);
+    if (!valid_vw(p.vw) || p.kt < 1 || p.kt * PPR_LANES * p.vw > PPR_MAX_SLOTS) return cudaErrorInvalidValue;
+    switch (p.vw) {
+        case 1: ppr_fixups_kernel<1><<<grid, PPR_BLOCK, 0, st>>>(p); break;
+        case 2: ppr_fixups_kernel<2><<<grid, PPR_BLOCK, 0, st>>>(p); break;
+        default: ppr_fixups_kernel<4><<<grid, PPR_BLOCK, 0, st>>>(p); break;
+    }
     return cudaGetLastError();
 }
 
@@ -362,8 +515,8 @@ cudaError_t launch_ppr_seedbits(cudaStream_t st, int32_t nseeds, const int32_t* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32_t slot, float* out) {
-    ppr_extract_kernel<<<grid_1d(n), 256, 0, st>>>(n, r, slot, out);
+cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32_t width, int32_t slot, float* out) {
+    ppr_extract_kernel<<<grid_1d(n), 256, 0, st>>>(n, r, width, slot, out);
     return cudaGetLastError();
 }
 

@@ -216,3 +216,30 @@ def test_rmat20_k64_full_size(grb):
             assert np.all(r >= 0) and abs(r.sum() - 1.0) < 1e-4
     finally:
         _teardown(grb, ctx, AT, P)
+
+
+def test_vector_widths_give_identical_bits_and_tuner_picks_one(grb, graph12):
+    """Each lane carrying 1, 2 or 4 slots is a layout choice only: the ranks
+    are bit-identical; the autotuner times all three widths."""
+    n, src, dst = graph12[:3]
+    sets = graphgen.ppr_seed_sets(n, 40, 1, 32, seed=12)
+    ctx, AT, P = _setup(grb, n, src, dst, 40)
+    try:
+        ms, vw = grb.grb_ppr_tune(P, 2)
+        assert np.all(ms > 0) and vw in (1, 2, 4)
+        results = {}
+        for width in (1, 2, 4):
+            grb.grb_ppr_layout(P, width)
+            assert grb.grb_ppr_slots(P) == {1: 64, 2: 64, 4: 128}[width]
+            for s, S in enumerate(sets):
+                grb.grb_ppr_set(P, s, S, -1.0, 20)
+            grb.grb_ppr_run(P, 20)
+            results[width] = [grb.grb_ppr_get(P, s, n) for s in range(40)]
+        for s in range(40):
+            assert np.array_equal(results[1][s], results[2][s]) and np.array_equal(results[1][s], results[4][s]), s
+        ref, _, _ = _oracle_ppr(graph12, sets[7], 20)
+        assert np.sum(np.abs(results[4][7].astype(np.float64) - ref)) <= 1e-6
+        with pytest.raises(grb.GrbError):
+            grb.grb_ppr_layout(P, 3)
+    finally:
+        _teardown(grb, ctx, AT, P)
