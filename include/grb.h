@@ -130,10 +130,14 @@ typedef enum {
                                   loop's vectors are permuted in and out), so the
                                   rank gathers touch fewer cache lines; 0: the
                                   matrix as built */
-    GRB_OPT_HOT_BYTES = 7      /* bytes of shared memory per SM that the persistent
+    GRB_OPT_HOT_BYTES = 7,     /* bytes of shared memory per SM that the persistent
                                   FP32 loop on a degree-ordered matrix uses for a
                                   copy of the most-gathered rank entries
                                   (0 .. GRB_HOT_BYTES_MAX; default 131072; 0 = off) */
+    GRB_OPT_TMA_STAGES = 8     /* that loop's tile arrays: 0 (default) = register
+                                  prefetch one tile ahead; 2 or 3 = bulk copies
+                                  (cp.async.bulk) into shared-memory stages that
+                                  many tiles ahead (the hot copy shrinks to fit) */
 } grb_option;
 
 #define GRB_HOT_BYTES_MAX 196608

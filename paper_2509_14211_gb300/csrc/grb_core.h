@@ -181,6 +181,7 @@ struct Ctx {
     bool mixed = false;
     bool relabel = true;  // device loops run on the degree-ordered copy of the matrix
     int64_t hot_bytes = 128 * 1024;  // shared-memory copy of the hottest gathered entries
+    int32_t tma_stages = 0;          // bulk-copy staging depth of the hot loop (0: register prefetch)
     bool dry = false;     // replaying a loop body to inspect its DAG: never execute
     DevBuf red_scratch;   // per-block partials of the reduction kernels
     DevBuf red_counter;   // last-block counter of the reduction kernels
@@ -235,7 +236,8 @@ struct PrBatch;
 void prbatch_destroy(PrBatch* B);
 grb_info read_status(Ctx* c);
 PrParams plan_params_of(Ctx* c, Matrix* A);
-int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n = 0);
+int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n = 0,
+            int32_t tma_stages = 0);
 double round_host(grb_type t, double x);
 double host_binop(int32_t code, double k, double x, double y);
 bool guaranteed_full(const Version* v);

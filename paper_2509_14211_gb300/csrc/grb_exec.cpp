@@ -317,8 +317,9 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
 
 PrParams plan_params_of(Ctx* c, Matrix* A) { return plan_params(c, A); }
 
-int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n) {
-    int nb = pr_blocks_per_sm(T, G, gmode, persistent, hot_n);
+int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n,
+            int32_t tma_stages) {
+    int nb = pr_blocks_per_sm(T, G, gmode, persistent, hot_n, tma_stages);
     if (nb <= 0) {
         if (persistent == 1 && hot_n > 0) return 0;   // the hot-copy kernel cannot run: caller drops it
         nb = 1;

@@ -337,11 +337,19 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     if (!st && mode == 1) {
         // shared-memory copy of the hottest entries of w: only useful when
         // the vertices are in degree order
-        if (rel && !mixed && T == GRB_FP32 && c->hot_bytes >= 16)
-            p.hot_n = (int32_t)(std::min<int64_t>(n, c->hot_bytes / (int64_t)sizeof(float)) & ~(int64_t)3);
-        int grid = p.hot_n > 0 ? pr_grid(c, AL, T, G, G_W, 1, p.hot_n) : 0;
+        if (rel && !mixed && T == GRB_FP32 && c->hot_bytes >= 16) {
+            // the staging buffers share the block's shared memory with the copy
+            p.tma_stages = c->tma_stages;
+            const int64_t stage_b = (int64_t)pr_hot_dynamic_smem(0, p.tma_stages);
+            const int64_t room = (int64_t)PR_SMEM_PER_BLOCK_MAX - (int64_t)PR_HOT_STATIC_SMEM - stage_b;
+            const int64_t bytes = std::min<int64_t>(c->hot_bytes, room);
+            p.hot_n = (int32_t)(std::min<int64_t>(n, bytes / (int64_t)sizeof(float)) & ~(int64_t)3);
+            if (p.hot_n <= 0) p.tma_stages = 0;
+        }
+        int grid = p.hot_n > 0 ? pr_grid(c, AL, T, G, G_W, 1, p.hot_n, p.tma_stages) : 0;
         if (grid <= 0) {
             p.hot_n = 0;
+            p.tma_stages = 0;
             grid = pr_grid(c, AL, T, G, G_W, 1);
         }
         c->stats.kernel_launches++;

@@ -171,6 +171,9 @@ struct PrParams {
     // persistent loop: gathers of columns < hot_n are served from a copy of
     // w[0, hot_n) in shared memory (multiple of 4; 0 = off; FP32 only)
     int32_t hot_n = 0;
+    // hot persistent loop: tile arrays staged by bulk copies this many tiles
+    // ahead (0 = register prefetch one tile ahead; 2 or 3)
+    int32_t tma_stages = 0;
     // batch of independent graphs (block-diagonal A^T): per-row graph id,
     // per-graph loop state and teleport, per-row residual / dangling terms
     const int32_t* graph_of = nullptr;
@@ -402,7 +405,13 @@ cudaError_t launch_mg_graph_of(cudaStream_t st, int32_t ngraphs, const int64_t* 
 // Resident CTAs per SM of the fused kernel for the given rank / gather types
 // (hot_n > 0: the persistent kernel with a hot copy of hot_n entries; 0 when
 // that configuration cannot run).
-int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n = 0);
+int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n = 0,
+                     int32_t tma_stages = 0);
+// Dynamic shared memory of the hot persistent kernel.
+size_t pr_hot_dynamic_smem(int32_t hot_n, int32_t tma_stages);
+// Static shared memory of the hot persistent kernel (bytes, upper bound).
+constexpr size_t PR_HOT_STATIC_SMEM = 34 * 1024;
+constexpr size_t PR_SMEM_PER_BLOCK_MAX = 227 * 1024;
 // Threads per CTA of the persistent kernel with the shared-memory hot copy
 // (one CTA per SM).
 constexpr int PR_HOT_BLOCK = 1024;

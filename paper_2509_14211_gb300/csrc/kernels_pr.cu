@@ -490,6 +490,123 @@ __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& i
     empty_rows<T, G, NC, EPI>(p, io, resid, dang);
 }
 
+// ------------------------------------------------ bulk-copy staging of tiles
+// The persistent loop can stream the per-tile arrays (256 column indices and
+// the 8 row-end words of a tile, 1056 bytes) into shared memory with
+// cp.async.bulk, PR_TMA_STAGES tiles ahead of the warp that will use them;
+// each stage has an mbarrier that the copy completes.  The warp's lane 0
+// issues the copies; every wait is bounded.
+struct alignas(16) TmaStage {
+    int32_t cols[PR_NZTILE];
+    uint32_t bits[PR_NZTILE / 32];
+};
+constexpr uint32_t TMA_STAGE_BYTES = sizeof(TmaStage);
+static_assert(TMA_STAGE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of a stage's barrier.
+__device__ __forceinline__ bool stage_wait(uint64_t* b, uint32_t parity, int64_t limit) {
+    for (int64_t spins = 0; !mbar_try_wait(b, parity); ++spins)
+        if (spins > limit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void stage_issue(const PrParams& p, int t, TmaStage* st, uint64_t* b) {
+    mbar_expect_tx(b, TMA_STAGE_BYTES);
+    bulk_to_smem(st->cols, p.col_idx + (size_t)t * PR_NZTILE, PR_NZTILE * sizeof(int32_t), b);
+    bulk_to_smem(st->bits, p.rowend_bits + (size_t)t * (PR_NZTILE / 32), (PR_NZTILE / 32) * sizeof(uint32_t), b);
+}
+
+// Phase A with the tile arrays staged by bulk copies.  `seq` counts the
+// tiles this warp has consumed in the launch (it selects the stage and the
+// barrier phase) and carries over from body to body.
+template <class T, class G, int GMODE, int EPI, bool HOT, int NW, int NST>
+__device__ __forceinline__ void phase_a_tma(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                            Smem<T, NW>& sm, TmaStage* stages, uint64_t* bars, uint32_t& seq) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * NW;
+    const int w0 = blockIdx.x * NW + warp;
+    const int count = w0 < p.ntiles ? (p.ntiles - w0 + nwarps - 1) / nwarps : 0;
+    TmaStage* S = stages + warp * NST;
+    uint64_t* B = bars + warp * NST;
+    if (lane == 0)
+        for (int k = 0; k < count && k < NST; ++k) stage_issue(p, w0 + k * nwarps, S + (seq + k) % NST, B + (seq + k) % NST);
+    __syncwarp();
+    auto first_row = [&](uint32_t meta) {
+        const int rfirst = (int)(meta & 0x7fffffffu);
+        return rfirst + lane < p.n_ne ? ld_stream(p.ne_rows + rfirst + lane) : -1;
+    };
+    uint32_t meta_cur = count > 0 ? __ldg(p.tile_meta + w0) : 0u;
+    uint32_t meta_next = count > 1 ? __ldg(p.tile_meta + w0 + nwarps) : 0u;
+    int pre_cur = count > 0 ? first_row(meta_cur) : -1;
+    int k = 0;
+    for (; k < count; ++k) {
+        const int t = w0 + k * nwarps;
+        const uint32_t u = seq + (uint32_t)k;
+        const int s = (int)(u % NST);
+        if (!stage_wait(B + s, (u / NST) & 1u, p.spin_limit)) {
+            set_status(p.status, (int32_t)GRB_DEVICE_TIMEOUT);
+            break;
+        }
+        TilePre f;
+        f.meta = meta_cur;
+        f.pre_i = pre_cur;
+        f.ca = *reinterpret_cast<const int4*>(S[s].cols + lane * PR_NZLANE);
+        f.cb = *reinterpret_cast<const int4*>(S[s].cols + lane * PR_NZLANE + 4);
+        f.bits = S[s].bits[lane >> 2];
+        __syncwarp();
+        if (lane == 0 && k + NST < count) {
+            // the warp's reads of this stage come before the copy's writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            stage_issue(p, t + NST * nwarps, S + s, B + s);
+        }
+        if (k + 1 < count) {
+            meta_cur = meta_next;
+            meta_next = k + 2 < count ? __ldg(p.tile_meta + t + 2 * nwarps) : 0u;
+            pre_cur = first_row(meta_cur);
+        }
+        warp_tile<T, G, GMODE, false, EPI, HOT>(p, t, f, io, resid, dang, sm.w[warp]);
+    }
+    if (k < count) {
+        // a wait ran out: let this warp's copies still in flight land (again
+        // bounded) before the kernel leaves at the next grid barrier
+        for (int q = k; q < count && q < k + NST; ++q) {
+            const uint32_t u = seq + (uint32_t)q;
+            stage_wait(B + u % NST, (u / NST) & 1u, p.spin_limit);
+        }
+    }
+    seq += (uint32_t)count;
+    empty_rows<T, G, false, EPI>(p, io, resid, dang);
+}
+
 template <class T>
 __device__ __forceinline__ T tele_value(const PrParams& p) {
     return p.tele_from_slot ? (T)round_to(p.out.type, *p.tele_slot) : (T)p.tele_const;
@@ -573,11 +690,22 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 // are the most-gathered entries (for R-MAT, the first 32K of 4M vertices
 // take about half of all gathers), so half of the random gathers never reach
 // L1/L2; the copy costs hot_n words per CTA per body from L2.
-template <class T, class G, int BLK, bool HOT>
+template <class T, class G, int BLK, bool HOT, int NST = 0>
 __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
     pr_persistent_kernel(const __grid_constant__ PrParams p) {
     __shared__ Smem<T, BLK / 32> sm;
     extern __shared__ int4 hot_raw[];
+    // dynamic shared memory: [hot copy (hot_n words)][NST tile stages per
+    // warp][NST barriers per warp]
+    TmaStage* stages = reinterpret_cast<TmaStage*>(reinterpret_cast<char*>(hot_raw) + (size_t)p.hot_n * sizeof(G));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (BLK / 32) * (NST > 0 ? NST : 1));
+    uint32_t seq = 0;
+    if constexpr (NST > 0) {
+        if ((threadIdx.x & 31) == 0)
+            for (int q = 0; q < NST; ++q) mbar_init(bars + (threadIdx.x >> 5) * NST + q, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        __syncwarp();
+    }
     const int G_ = gridDim.x;
     const T* dd = reinterpret_cast<const T*>(p.dd);
     const T* r0 = reinterpret_cast<const T*>(p.r0);
@@ -626,7 +754,10 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
             __syncthreads();
         }
         Acc<T> racc, dacc;
-        phase_a<T, G, G_W, false, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
+        if constexpr (NST > 0)
+            phase_a_tma<T, G, G_W, EPI_LEAN, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
+        else
+            phase_a<T, G, G_W, false, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
         fixups<T, G, false, EPI_LEAN>(p, io, racc, dacc);
         const double resid = block_sum_d<BLK>(racc.value(), sm.red);
@@ -850,9 +981,15 @@ void* pick_kernel(int32_t rank_type, int32_t gather_type, int32_t gmode, int per
 // The persistent loop with the shared-memory copy of the hottest gathered
 // entries: FP32 ranks and gathers only (the FP64 kernel's row-sum slices for
 // 32 warps would exceed the static shared-memory limit).
-void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn) {
+void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn, int32_t nst) {
     if (rank_type != GRB_FP32 || gather_type != GRB_FP32) return nullptr;
-    void* k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true>;
+    void* k = nullptr;
+    switch (nst) {
+        case 0: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 0>; break;
+        case 2: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 2>; break;
+        case 3: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 3>; break;
+        default: return nullptr;
+    }
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) return nullptr;
     return k;
 }
@@ -894,14 +1031,19 @@ cudaError_t launch_mg_graph_of(cudaStream_t st, int32_t ngraphs, const int64_t* 
     return cudaGetLastError();
 }
 
-int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n) {
+size_t pr_hot_dynamic_smem(int32_t hot_n, int32_t tma_stages) {
+    return (size_t)hot_n * sizeof(float) + (size_t)(PR_HOT_BLOCK / 32) * tma_stages * (TMA_STAGE_BYTES + 8);
+}
+
+int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n,
+                     int32_t tma_stages) {
     int block = PR_BLOCK;
     size_t dyn = 0;
     void* k = nullptr;
     if (persistent == 1 && hot_n > 0) {
-        dyn = (size_t)hot_n * sizeof(float);
+        dyn = pr_hot_dynamic_smem(hot_n, tma_stages);
         block = PR_HOT_BLOCK;
-        k = pick_hot(rank_type, gather_type, dyn);
+        k = pick_hot(rank_type, gather_type, dyn, tma_stages);
     } else {
         k = pick_kernel(rank_type, gather_type, gmode, persistent == 1, persistent == 2);
     }
@@ -917,8 +1059,8 @@ cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int
     // iterated sequence
     const bool hot = persistent == 1 && p.hot_n > 0;
     if (hot && (p.hot_n % 4 != 0 || p.hot_n > p.nrows || p.mixed)) return cudaErrorInvalidValue;
-    const size_t dyn = hot ? (size_t)p.hot_n * sizeof(float) : 0;
-    void* k = hot ? pick_hot(rank_type, gather_type, dyn)
+    const size_t dyn = hot ? pr_hot_dynamic_smem(p.hot_n, p.tma_stages) : 0;
+    void* k = hot ? pick_hot(rank_type, gather_type, dyn, p.tma_stages)
                   : pick_kernel(rank_type, gather_type, p.gmode, persistent == 1, persistent == 2);
     if (!k) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};

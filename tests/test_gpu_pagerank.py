@@ -28,7 +28,7 @@ def grb():
 
 
 def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, persistent=0, fusion=True,
-         mixed=False, relabel=True, hot_bytes=None):
+         mixed=False, relabel=True, hot_bytes=None, tma=0):
     from paper_2509_14211_gb300.pagerank import pagerank
 
     ctx = grb.grb_context_new(mode if mode is not None else grb.GRB_NONBLOCKING)
@@ -38,6 +38,7 @@ def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, p
     grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 1 if relabel else 0)
     if hot_bytes is not None:
         grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, hot_bytes)
+    grb.grb_context_set(ctx, grb.GRB_OPT_TMA_STAGES, tma)
     try:
         r, it = pagerank(ctx, n, src, dst, damping=D, tol=tol, itermax=itermax, rank_type=rank_type,
                          dangling=dangling, loop=loop)
@@ -89,11 +90,13 @@ def test_fp32_fixed_iterations_scale16(grb, dangling):
     # persistent kernel with the default, no, a partial-warp-sized and the
     # largest shared-memory hot copy (n = 65536: the largest covers 3/4 of
     # the vertices); the CUDA-graph loop; both on the input vertex order
-    for persistent, relabel, hot in ((1, True, None), (1, True, 0), (1, True, 1040),
-                                     (1, True, grb.GRB_HOT_BYTES_MAX), (2, True, None), (1, False, None),
-                                     (2, False, None)):
+    # and the tile arrays staged by bulk copies 2 and 3 tiles ahead
+    for persistent, relabel, hot, tma in ((1, True, None, 0), (1, True, 0, 0), (1, True, 1040, 0),
+                                          (1, True, grb.GRB_HOT_BYTES_MAX, 0), (2, True, None, 0),
+                                          (1, False, None, 0), (2, False, None, 0), (1, True, None, 2),
+                                          (1, True, None, 3), (1, True, 1040, 3)):
         r, it, _, (hist, _) = _run(grb, n, src, dst, grb.GRB_FP32, dangling, "device", -1.0, 50,
-                                   persistent=persistent, relabel=relabel, hot_bytes=hot)
+                                   persistent=persistent, relabel=relabel, hot_bytes=hot, tma=tma)
         assert it == 50
         assert np.sum(np.abs(r - ref)) <= 1e-6
         # FP32 ranks put a noise floor of ~n * eps32 * mean(r) ~ 1e-8 under
@@ -108,10 +111,11 @@ def test_fp32_full_size_rmat22(grb):
     residual, 50 fixed iterations: the benchmark configuration."""
     n = 1 << 22
     src, dst = graphgen.rmat_edges(22, 16, seed=1)
-    r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", -1.0, 50, persistent=1)
     ref, k, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=50, mode="uniform")
-    assert it == 50 == k
-    assert np.sum(np.abs(r - ref)) <= 1e-6
+    for tma in (0, 2):
+        r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", -1.0, 50, persistent=1, tma=tma)
+        assert it == 50 == k
+        assert np.sum(np.abs(r - ref)) <= 1e-6
     assert abs(np.sum(r) - 1.0) < 1e-4 and np.all(r >= 0)
 
 
