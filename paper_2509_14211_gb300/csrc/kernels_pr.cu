@@ -294,7 +294,10 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
 template <class T, class G, int GMODE, bool NC, bool HOT = false>
 __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int j) {
     if constexpr (HOT) {
-        if (j < io.hot_n) return (T)io.hot[j];
+        // one generic load from shared memory (hot copy) or global memory,
+        // chosen per lane without a branch
+        const G* src = j < io.hot_n ? io.hot + j : io.w + j;
+        return (T)*src;
     }
     if (GMODE == G_W) {
         if (io.phase32) return (T)gload_f<float, NC>(io.w32, j);
@@ -366,7 +369,12 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePr
     const int cols[PR_NZLANE] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
     T v[PR_NZLANE];
 #pragma unroll
-    for (int q = 0; q < PR_NZLANE; ++q) v[q] = q < nvalid ? gather<T, G, GMODE, NC, HOT>(p, io, cols[q]) : (T)0;
+    for (int q = 0; q < PR_NZLANE; ++q) {
+        // padding entries of the last tile hold column 0: the load is in
+        // bounds, and its value is discarded
+        const T g = gather<T, G, GMODE, NC, HOT>(p, io, cols[q]);
+        v[q] = q < nvalid ? g : (T)0;
+    }
 
     // ---- row numbering: rows ending before this lane's nonzeros
     const int cnt = __popc(myf);
