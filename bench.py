@@ -222,6 +222,7 @@ def run_profile_case_batch(args):
         graphs.append((1 << scale, src, dst))
     n, src, dst, vptr = grb.block_diagonal_edges(graphs)
     ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 0 if args.no_relabel else 1)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     B = grb.grb_prbatch_new(AT, vptr, DAMPING)

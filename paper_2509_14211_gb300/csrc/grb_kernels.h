@@ -297,6 +297,10 @@ struct RelabelArgs {
 cudaError_t relabel_order(cudaStream_t st, const RelabelArgs& a, unsigned long long* top_sum, AllocFn af, FreeFn ff,
                           void* actx);
 cudaError_t relabel_build(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx);
+// Renumbering inside blocks: vertices sorted by (block[i], descending column
+// count of A^T, id), so every block keeps its index range (synchronises).
+cudaError_t block_degree_order(cudaStream_t st, int32_t n, const int32_t* col_idx, int64_t nnz, const int32_t* block,
+                               int32_t* new2old, int32_t* old2new, AllocFn af, FreeFn ff, void* actx);
 // out[k] = in[perm[k]] for 4- or 8-byte elements.
 cudaError_t launch_permute(cudaStream_t st, int32_t n, const int32_t* perm, const void* in, void* out, int32_t esize);
 // bit k of out = bit new2old[k] of in.

@@ -23,7 +23,9 @@ namespace grb {
 struct PrBatch {
     Kind kind = Kind::PRBATCH;
     Ctx* c = nullptr;
-    Matrix* A = nullptr;
+    Matrix* A = nullptr;       // the matrix the kernels run on (A_in, or its copy renumbered inside the blocks)
+    Matrix* A_in = nullptr;    // the caller's matrix
+    std::vector<int32_t> old2new_h;   // empty: no renumbering
     int32_t ng = 0;
     int64_t n = 0;
     double damping = 0.85;
@@ -203,7 +205,8 @@ void prbatch_destroy(PrBatch* B) {
     for (DevBuf* b : {&B->vptr, &B->graph_of, &B->dd, &B->sinkbits, &B->row_res, &B->row_dang, &B->r[0], &B->r[1],
                       &B->w[0], &B->w[1], &B->active, &B->iters, &B->resid, &B->tele, &B->final_buf})
         buf_free(c, *b);
-    matrix_unref(B->A);
+    if (B->A && B->A != B->A_in) matrix_unref(B->A);
+    matrix_unref(B->A_in);
     B->kind = Kind::DEAD;
     delete B;
 }
@@ -230,6 +233,7 @@ grb_info grb_prbatch_new(grb_prbatch* out, grb_matrix Am, int32_t ngraphs, const
     PrBatch* B = new PrBatch();
     B->c = c;
     B->A = A;
+    B->A_in = A;
     A->refs++;
     B->ng = ngraphs;
     B->n = A->nrows;
@@ -272,10 +276,73 @@ grb_info grb_prbatch_new(grb_prbatch* out, grb_matrix Am, int32_t ngraphs, const
                                  "graph ids");
         if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "batch setup");
     }
+    if (!st && nbad) st = GRB_INVALID_VALUE;   // an edge between two graphs
+    // Renumber each graph's vertices by descending out-degree inside its own
+    // block (the block-diagonal structure stays): the most-gathered entries
+    // of w become neighbours, as for the single-graph loop.
+    if (!st && c->relabel) {
+        auto af = [](void* x, size_t b2) { return dev_alloc((Ctx*)x, b2); };
+        auto ff = [](void* x, void* q, size_t b2) { dev_free((Ctx*)x, q, b2); };
+        DevBuf n2o = buf_alloc(c, sizeof(int32_t) * n), o2n = buf_alloc(c, sizeof(int32_t) * n);
+        Matrix* R = new Matrix();
+        R->ctx = c;
+        R->type = A->type;
+        R->nrows = A->nrows;
+        R->ncols = A->ncols;
+        R->nnz = A->nnz;
+        R->iso_val = A->iso_val;
+        R->nonempty_rows = A->nonempty_rows;
+        R->row_ptr = buf_alloc(c, sizeof(int32_t) * (size_t)(n + 1));
+        R->col_idx = buf_alloc(c, sizeof(int32_t) * (size_t)padded_nnz(A->nnz));
+        if (!n2o.p || !o2n.p || !R->row_ptr.p || !R->col_idx.p) st = GRB_OUT_OF_MEMORY;
+        if (!st) {
+            c->stats.kernel_launches += 4;
+            st = cuda_check(c, block_degree_order(c->stream, (int32_t)n, (const int32_t*)A->col_idx.p, A->nnz,
+                                                  (const int32_t*)B->graph_of.p, (int32_t*)n2o.p, (int32_t*)o2n.p, af,
+                                                  ff, c), "block order");
+        }
+        if (!st) {
+            RelabelArgs ra;
+            ra.n = (int32_t)n;
+            ra.nnz = A->nnz;
+            ra.row_ptr = (const int32_t*)A->row_ptr.p;
+            ra.col_idx = (const int32_t*)A->col_idx.p;
+            ra.new_row_ptr = (int32_t*)R->row_ptr.p;
+            ra.new_col_idx = (int32_t*)R->col_idx.p;
+            ra.new2old = (int32_t*)n2o.p;
+            ra.old2new = (int32_t*)o2n.p;
+            ra.top_h = 0;
+            c->stats.kernel_launches += 3;
+            st = cuda_check(c, relabel_build(c->stream, ra, af, ff, c), "block relabel");
+        }
+        if (!st) {
+            B->old2new_h.resize(n);
+            st = cuda_check(c, cudaMemcpy(B->old2new_h.data(), o2n.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost),
+                            "block relabel");
+        }
+        buf_free(c, n2o);
+        buf_free(c, o2n);
+        if (!st) st = ensure_plan(c, R);
+        if (st) {
+            matrix_unref(R);
+            B->old2new_h.clear();
+        } else {
+            B->A = R;
+            // graph ids and divisors in the new numbering
+            c->stats.kernel_launches += 4;
+            st = cuda_check(c, launch_mg_graph_of(c->stream, ngraphs, (const int64_t*)B->vptr.p, (int32_t)n,
+                                                  (const int32_t*)R->row_ptr.p, (const int32_t*)R->col_idx.p,
+                                                  (int32_t*)B->graph_of.p, (unsigned long long*)bad.p), "graph ids");
+            if (!st) st = cuda_check(c, launch_col_degree(c->stream, n, R->nnz, (const int32_t*)R->col_idx.p,
+                                                          (int32_t*)deg.p, (uint8_t*)pres.p), "out-degree");
+            if (!st) st = cuda_check(c, launch_ppr_divisor(c->stream, (int32_t)n, (const int32_t*)deg.p, damping,
+                                                           (float*)B->dd.p, (uint32_t*)B->sinkbits.p), "divisor");
+            if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "batch setup");
+        }
+    }
     buf_free(c, deg);
     buf_free(c, pres);
     buf_free(c, bad);
-    if (!st && nbad) st = GRB_INVALID_VALUE;   // an edge between two graphs
     if (st) {
         prbatch_destroy(B);
         return st;
@@ -354,8 +421,12 @@ grb_info grb_prbatch_result(grb_prbatch Bh, float* ranks, int64_t* iters, double
         if (st) return st;
         for (int32_t g = 0; g < B->ng; ++g) {
             const int src = act[g] ? B->cur : (fb[g] & 1);
-            std::memcpy(ranks + B->vptr_h[g], h[src].data() + B->vptr_h[g],
-                        sizeof(float) * (size_t)(B->vptr_h[g + 1] - B->vptr_h[g]));
+            if (B->old2new_h.empty()) {
+                std::memcpy(ranks + B->vptr_h[g], h[src].data() + B->vptr_h[g],
+                            sizeof(float) * (size_t)(B->vptr_h[g + 1] - B->vptr_h[g]));
+            } else {
+                for (int64_t i = B->vptr_h[g]; i < B->vptr_h[g + 1]; ++i) ranks[i] = h[src][B->old2new_h[i]];
+            }
         }
     }
     for (int32_t g = 0; g < B->ng; ++g) {

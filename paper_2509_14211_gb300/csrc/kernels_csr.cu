@@ -429,6 +429,40 @@ cudaError_t degree_order(cudaStream_t st, int32_t n, const int32_t* deg, int32_t
     return cudaStreamSynchronize(st);
 }
 
+__global__ void block_degree_keys_kernel(int32_t n, const int32_t* __restrict__ deg, const int32_t* __restrict__ block,
+                                         unsigned long long* keys, int32_t* ids) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        // ascending key: block first, then descending degree; ties keep the id order
+        keys[i] = ((unsigned long long)(uint32_t)block[i] << 32) | (unsigned long long)(uint32_t)(0x7fffffff - deg[i]);
+        ids[i] = i;
+    }
+}
+
+cudaError_t block_degree_order(cudaStream_t st, int32_t n, const int32_t* col_idx, int64_t nnz, const int32_t* block,
+                               int32_t* new2old, int32_t* old2new, AllocFn af, FreeFn ff, void* actx) {
+    Scratch S{af, ff, actx, {}};
+    cudaError_t e;
+    int32_t* deg = (int32_t*)S.get(sizeof(int32_t) * n);
+    unsigned long long* keys = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
+    unsigned long long* keys_out = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
+    int32_t* ids = (int32_t*)S.get(sizeof(int32_t) * n);
+    if (!deg || !keys || !keys_out || !ids) return cudaErrorMemoryAllocation;
+    if ((e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st)) != cudaSuccess) return e;
+    if (nnz > 0) col_count_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, col_idx, deg);
+    block_degree_keys_kernel<<<grid_for(n), 256, 0, st>>>(n, deg, block, keys, ids);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    size_t tb = 0;
+    if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tb, keys, keys_out, ids, new2old, n, 0, 64, st)) != cudaSuccess)
+        return e;
+    void* tmp = S.get(tb);
+    if (!tmp) return cudaErrorMemoryAllocation;
+    if ((e = cub::DeviceRadixSort::SortPairs(tmp, tb, keys, keys_out, ids, new2old, n, 0, 64, st)) != cudaSuccess)
+        return e;
+    invert_perm_kernel<<<grid_for(n), 256, 0, st>>>(n, new2old, old2new);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
 cudaError_t relabel_order(cudaStream_t st, const RelabelArgs& a, unsigned long long* top_sum, AllocFn af, FreeFn ff,
                           void* actx) {
     Scratch S{af, ff, actx, {}};
