@@ -664,10 +664,13 @@ def main():
     grb.grb_free(AT)
     grb.grb_free(ctx)
 
-    mixed_leg = run_mixed_leg(grb, torch, stream) if not args.no_mixed else None
-    ppr_leg = run_ppr_leg(grb, torch, stream) if not args.no_ppr else None
-    serve_leg = run_serve_leg(grb) if not args.no_serve else None
-    batch_leg = run_batch_leg(grb, torch, stream) if not args.no_batch else None
+    # the extension legs are single-GPU measurements: with several ranks only
+    # the replicated main metric runs, so the N GPUs are held no longer
+    legs = ws == 1
+    mixed_leg = run_mixed_leg(grb, torch, stream) if legs and not args.no_mixed else None
+    ppr_leg = run_ppr_leg(grb, torch, stream) if legs and not args.no_ppr else None
+    serve_leg = run_serve_leg(grb) if legs and not args.no_serve else None
+    batch_leg = run_batch_leg(grb, torch, stream) if legs and not args.no_batch else None
 
     # ---------------------------------------------------------- roofline
     # algorithmic bytes of one launch of the persistent kernel: per body
@@ -713,7 +716,7 @@ def main():
         "graph_batch_512": batch_leg,
         "wall_s_timed_region": t_wall,
     }
-    if rank == 0 and not args.no_oracle:
+    if ws == 1 and not args.no_oracle:   # the CPU baseline: one process, N = 1 only
         import oracle
 
         t0 = time.perf_counter()
