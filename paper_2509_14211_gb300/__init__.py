@@ -216,10 +216,12 @@ def _acc(accum):
 
 
 # ---------------------------------------------------------------- context
-def grb_context_new(mode: int = GRB_NONBLOCKING, stream=None, torch_allocator: bool = True) -> int:
+def grb_context_new(mode: int = GRB_NONBLOCKING, stream=None, torch_allocator: bool = True, alloc_hook=None) -> int:
     """New context on the current CUDA device.  `stream` is a torch CUDA
     stream (default: torch's current stream).  With torch_allocator, device
-    memory comes from torch's caching allocator."""
+    memory comes from torch's caching allocator; alloc_hook(nbytes) -> bool,
+    when given, is asked before every allocation and a False answer makes
+    that allocation fail (allocator-failure injection)."""
     import torch
     lib = load()
     if not torch.cuda.is_available():
@@ -229,6 +231,8 @@ def grb_context_new(mode: int = GRB_NONBLOCKING, stream=None, torch_allocator: b
     handle = ctypes.c_void_p(st.cuda_stream)
     if torch_allocator:
         def _alloc(_ctx, nbytes, stream_ptr):
+            if alloc_hook is not None and not alloc_hook(int(nbytes)):
+                return None
             try:
                 return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream_ptr or 0))
             except Exception:

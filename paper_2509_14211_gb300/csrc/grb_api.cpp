@@ -288,6 +288,7 @@ grb_info grb_context_wait(grb_context ctx) {
 grb_info grb_matrix_build_csr(grb_matrix* Aout, grb_context ctx, grb_type type, uint64_t nrows, uint64_t ncols,
                               const int32_t* src, const int32_t* dst, const void* vals, uint64_t nedges,
                               uint32_t flags) {
+    NvtxRange range("grb: CSR build");
     if (!Aout) return GRB_NULL_POINTER;
     *Aout = nullptr;
     Ctx* c = as_ctx(ctx);

@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "grb.h"
 #include "grb_kernels.h"
 
@@ -197,6 +199,15 @@ struct Ctx {
     int last_mixed_phase = -1;
     std::vector<VectorH*> vhandles;   // live handles (grb_context_wait completes them)
     std::vector<ScalarH*> shandles;
+};
+
+// Profiler range for the duration of a scope (NVTX; free when no profiler
+// is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // ------------------------------------------------------------- memory

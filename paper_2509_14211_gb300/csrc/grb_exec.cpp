@@ -132,6 +132,17 @@ static void sem_ops(grb_semiring s, int32_t& add, int32_t& mul) {
     }
 }
 
+static void plan_free(Ctx* c, TilePlan* p) {
+    for (DevBuf* b : {&p->meta, &p->rowend_bits, &p->ne_rows, &p->empty_rows, &p->agg, &p->first, &p->fix,
+                      &p->longfix, &p->part, &p->sync})
+        buf_free(c, *b);
+    for (auto& b : p->loop_bufs) buf_free(c, b);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    delete p;
+}
+
+// The matrix's row plan, built once; nothing is cached unless the whole plan
+// was built.
 grb_info ensure_plan(Ctx* c, Matrix* A) {
     if (A->plan) return GRB_SUCCESS;
     TilePlan* p = new TilePlan();
@@ -147,10 +158,11 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
     p->longfix = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 3));
     p->part = buf_alloc(c, sizeof(double) * 2 * 2 * (size_t)c->sm_count * 8);
     p->sync = buf_alloc(c, sizeof(SyncWords));
-    A->plan = p;
     if (!p->meta.p || !p->rowend_bits.p || !p->ne_rows.p || !p->empty_rows.p || !p->agg.p || !p->first.p ||
-        !p->fix.p || !p->longfix.p || !p->part.p || !p->sync.p)
+        !p->fix.p || !p->longfix.p || !p->part.p || !p->sync.p) {
+        plan_free(c, p);
         return GRB_OUT_OF_MEMORY;
+    }
     int32_t* counts_dev = (int32_t*)p->longfix.p + p->ntiles;
     PlanArgs pa;
     pa.row_ptr = (const int32_t*)A->row_ptr.p;
@@ -167,16 +179,22 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
     grb_info st = cuda_check(c, build_row_plan(c->stream, pa, [](void* x, size_t b) { return dev_alloc((Ctx*)x, b); },
                                                [](void* x, void* q, size_t b) { dev_free((Ctx*)x, q, b); }, c),
                              "row plan");
-    if (st) return st;
     c->stats.kernel_launches += 5;
     int32_t counts[3] = {0, 0, 0};
-    st = cuda_check(c, cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, c->stream), "plan");
+    if (!st)
+        st = cuda_check(c, cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, c->stream), "plan");
     if (!st) st = cuda_check(c, cudaMemsetAsync(p->sync.p, 0, sizeof(SyncWords), c->stream), "plan sync");
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "plan");
+    if (st) {
+        cudaStreamSynchronize(c->stream);
+        plan_free(c, p);
+        return st;
+    }
     p->n_ne = counts[0];
     p->n_empty = counts[1];
     p->nlong = counts[2];
-    return st;
+    A->plan = p;
+    return GRB_SUCCESS;
 }
 
 // Degree-ordered copy of a square pattern matrix, built once and cached on
@@ -261,6 +279,7 @@ grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits) {
     if (bits) {
         if (v->perm_bits_key == A->rel_id && v->perm_sinkbits.p) return GRB_SUCCESS;
         buf_free(c, v->perm_sinkbits);
+        v->perm_bits_key = 0;
         v->perm_sinkbits = buf_alloc(c, sizeof(uint32_t) * (size_t)((n + 31) / 32));
         if (!v->perm_sinkbits.p) return GRB_OUT_OF_MEMORY;
         c->stats.kernel_launches++;
@@ -272,6 +291,7 @@ grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits) {
     if (v->fmt != Fmt::FULL) return GRB_INVALID_VALUE;
     if (v->perm_vals_key == A->rel_id && v->perm_vals.p) return GRB_SUCCESS;
     buf_free(c, v->perm_vals);
+    v->perm_vals_key = 0;
     v->perm_vals = buf_alloc(c, type_size(v->type) * (size_t)n);
     if (!v->perm_vals.p) return GRB_OUT_OF_MEMORY;
     c->stats.kernel_launches++;
@@ -283,10 +303,17 @@ grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits) {
 
 grb_info ensure_sinkbits(Ctx* c, Version* s) {
     if (s->sinkbits.p) return GRB_SUCCESS;
-    s->sinkbits = buf_alloc(c, sizeof(uint32_t) * (size_t)((s->n + 31) / 32));
-    if (!s->sinkbits.p) return GRB_OUT_OF_MEMORY;
+    DevBuf b = buf_alloc(c, sizeof(uint32_t) * (size_t)((s->n + 31) / 32));
+    if (!b.p) return GRB_OUT_OF_MEMORY;
     c->stats.kernel_launches++;
-    return cuda_check(c, launch_sinkbits(c->stream, s->n, vin_of(s), (uint32_t*)s->sinkbits.p), "sink bits");
+    grb_info st = cuda_check(c, launch_sinkbits(c->stream, s->n, vin_of(s), (uint32_t*)b.p), "sink bits");
+    if (st) {
+        cudaStreamSynchronize(c->stream);
+        buf_free(c, b);
+        return st;
+    }
+    s->sinkbits = b;   // cached only once built
+    return GRB_SUCCESS;
 }
 
 static PrParams plan_params(Ctx* c, Matrix* A) {
@@ -848,8 +875,11 @@ grb_info materialize(Ctx* c, Version* target) {
     }
     std::sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.root->seq < b.root->seq; });
 
+    NvtxRange range("grb: wait (fused groups)");
     grb_info st = GRB_SUCCESS;
     for (Group& g : groups) {
+        NvtxRange grange(g.kind == Group::PR ? "grb: PageRank group" : g.kind == Group::EWRED ? "grb: element-wise + reduce group"
+                                                                                           : "grb: single method");
         if (g.kind == Group::PR) st = exec_pr_group(c, C, g);
         else if (g.kind == Group::EWRED) {
             st = exec_reduce(c, g.red, g.ew, g.chain, g.root->out);

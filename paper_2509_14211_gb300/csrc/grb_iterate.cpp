@@ -227,6 +227,7 @@ grb_info replay_dry(Ctx* c, const std::vector<Stmt>& body) {
 
 static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond, LoopMatch& lm, double tol,
                             int64_t itermax, double rd0, int64_t* iters_out) {
+    NvtxRange range("grb: device PageRank loop");
     const grb_type T = lm.T;
     const bool mixed = c->mixed && T == GRB_FP32;
     const grb_type G = mixed ? GRB_BF16 : T;

@@ -404,6 +404,7 @@ grb_info grb_ppr_clear(grb_ppr Ph, int32_t slot) {
 }
 
 grb_info grb_ppr_run(grb_ppr Ph, int64_t iters) {
+    NvtxRange range("grb: personalised PageRank bodies");
     Ppr* P = as_ppr(Ph);
     if (!Ph) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;

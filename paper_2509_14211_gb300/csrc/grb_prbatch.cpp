@@ -364,6 +364,7 @@ grb_info grb_prbatch_tune(grb_prbatch Bh, int64_t trial_bodies, double* ms_per_b
 }
 
 grb_info grb_prbatch_run(grb_prbatch Bh, double tol, int64_t itermax, int64_t chunk) {
+    NvtxRange range("grb: graph batch solve");
     PrBatch* B = as_batch(Bh);
     if (!Bh) return GRB_NULL_POINTER;
     if (!B) return GRB_UNINITIALIZED_OBJECT;

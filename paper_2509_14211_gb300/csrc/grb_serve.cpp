@@ -97,6 +97,7 @@ grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, c
             }
             continue;
         }
+        NvtxRange step("grb: serving step");
         st = grb_ppr_run(P, cfg->chunk);
         if (!st) st = grb_ppr_status(P, active.data(), its.data(), res.data());
         if (st) break;

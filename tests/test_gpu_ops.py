@@ -300,3 +300,46 @@ def test_device_wait_timeout_is_reported_not_hung(grb, ctx):
     assert grb.grb_scalar_get(s) == 16.0
     grb.grb_free(v)
     grb.grb_free(s)
+
+
+def test_allocator_failure_is_reported_and_recoverable(grb):
+    """Allocator-failure injection: with the allocator refusing every
+    request, a method that needs new device memory fails with
+    GRB_OUT_OF_MEMORY at its wait (execution error, sticky on the output)
+    and the device loop fails the same way; once the allocator answers
+    again the context computes correct results."""
+    from paper_2509_14211_gb300.pagerank import PageRankProblem, build_graph
+
+    gate = {"open": True}
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING, alloc_hook=lambda nbytes: gate["open"])
+    try:
+        n = 1 << 12
+        src, dst = graphgen.rmat_edges(12, 8, seed=21)
+        AT = build_graph(ctx, n, src, dst)
+        u = grb.grb_vector_new(ctx, grb.GRB_FP64, 3 << 20)
+        grb.grb_vector_fill(u, 2.0)
+        gate["open"] = False
+        w = grb.grb_vector_new(ctx, grb.GRB_FP64, 3 << 20)
+        grb.grb_ewise_mult(w, None, None, grb.binop(grb.GRB_TIMES), u, u)   # recorded, not run
+        with pytest.raises(grb.GrbError) as e:
+            grb.grb_wait(w)
+        assert e.value.code == grb.GRB_OUT_OF_MEMORY
+        with pytest.raises(grb.GrbError) as e:
+            P = PageRankProblem(ctx, AT, n, 0.85, grb.GRB_FP32)
+            P.run(-1.0, 5)
+        assert e.value.code == grb.GRB_OUT_OF_MEMORY
+        gate["open"] = True
+        w2 = grb.grb_vector_new(ctx, grb.GRB_FP64, 3 << 20)
+        grb.grb_ewise_mult(w2, None, None, grb.binop(grb.GRB_TIMES), u, u)
+        vals, _ = grb.grb_vector_extract_dense(w2, grb.GRB_FP64)
+        assert np.all(vals == 4.0)
+        P2 = PageRankProblem(ctx, AT, n, 0.85, grb.GRB_FP32)
+        assert P2.run(-1.0, 5) == 5
+        ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=0.85, tol=-1.0, itermax=5, mode="uniform")
+        assert np.sum(np.abs(P2.rank().astype(np.float64) - ref)) <= 1e-6
+        for h in (w, w2, u):
+            grb.grb_free(h)
+        P2.free()
+        grb.grb_free(AT)
+    finally:
+        grb.grb_free(ctx)
