@@ -338,7 +338,9 @@ grb_info grb_ppr_slots(grb_ppr P, int32_t* slots);
 grb_info grb_ppr_tune(grb_ppr P, int64_t trial_bodies, double* ms_per_body, int32_t* chosen_vw);
 
 /* Set the vector width (1, 2 or 4) directly; empties every slot.  Results do
- * not depend on the width. */
+ * not depend on the width.  When a re-layout (here or in grb_ppr_tune) runs
+ * out of memory, the object answers GRB_INVALID_OBJECT to every other call
+ * until a re-layout succeeds. */
 grb_info grb_ppr_layout(grb_ppr P, int32_t vw);
 
 /* Start a query in `slot` (replacing whatever it held): seeds are host

@@ -35,6 +35,7 @@ struct Ppr {
     cudaGraphExec_t exec = nullptr;
     int64_t exec_iters = 0;
     int exec_cur = -1;
+    grb_info broken = GRB_SUCCESS;    // a failed re-layout: every later call returns it
 };
 
 namespace {
@@ -209,6 +210,7 @@ grb_info alloc_layout(Ppr* P, int32_t vw) {
                       &P->resid, &P->tele, &P->final_buf})
         if (!st) st = cuda_check(c, cudaMemsetAsync(b->p, 0, b->bytes, c->stream), "ppr layout");
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr layout");
+    P->broken = st;
     return st;
 }
 
@@ -283,7 +285,7 @@ grb_info grb_ppr_layout(grb_ppr Ph, int32_t vw) {
     if (!Ph) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
     if (vw != 1 && vw != 2 && vw != 4) return GRB_INVALID_VALUE;
-    return alloc_layout(P, vw);
+    return alloc_layout(P, vw);   // also the way out of a failed re-layout
 }
 
 grb_info grb_ppr_tune(grb_ppr Ph, int64_t trial_bodies, double* ms_per_body, int32_t* chosen_vw) {
@@ -333,6 +335,7 @@ grb_info grb_ppr_slots(grb_ppr Ph, int32_t* slots) {
     Ppr* P = as_ppr(Ph);
     if (!Ph || !slots) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (P->broken) return GRB_INVALID_OBJECT;
     *slots = P->slots;
     return GRB_SUCCESS;
 }
@@ -341,6 +344,7 @@ grb_info grb_ppr_set(grb_ppr Ph, int32_t slot, const int32_t* seeds, int64_t nse
     Ppr* P = as_ppr(Ph);
     if (!Ph || !seeds) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (P->broken) return GRB_INVALID_OBJECT;
     if (slot < 0 || slot >= P->slots || nseeds < 1 || itermax < 0 || itermax > INT32_MAX) return GRB_INVALID_VALUE;
     std::vector<int32_t> S(seeds, seeds + nseeds);
     for (int32_t v : S)
@@ -392,6 +396,7 @@ grb_info grb_ppr_clear(grb_ppr Ph, int32_t slot) {
     Ppr* P = as_ppr(Ph);
     if (!Ph) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (P->broken) return GRB_INVALID_OBJECT;
     if (slot < 0 || slot >= P->slots) return GRB_INVALID_VALUE;
     const int32_t zero = 0;
     grb_info st = cuda_check(P->c, cudaMemcpyAsync((int32_t*)P->active.p + slot, &zero, 4, cudaMemcpyHostToDevice,
@@ -408,6 +413,7 @@ grb_info grb_ppr_run(grb_ppr Ph, int64_t iters) {
     Ppr* P = as_ppr(Ph);
     if (!Ph) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (P->broken) return GRB_INVALID_OBJECT;
     if (iters < 0 || iters > 100000) return GRB_INVALID_VALUE;
     if (iters == 0) return GRB_SUCCESS;
     Ctx* c = P->c;
@@ -443,6 +449,7 @@ grb_info grb_ppr_status(grb_ppr Ph, int32_t* active, int64_t* iters, double* res
     Ppr* P = as_ppr(Ph);
     if (!Ph) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (P->broken) return GRB_INVALID_OBJECT;
     Ctx* c = P->c;
     const int S = P->slots;
     std::vector<int32_t> a(S), it(S);
@@ -467,6 +474,7 @@ grb_info grb_ppr_get(grb_ppr Ph, int32_t slot, float* ranks, int out_is_device) 
     Ppr* P = as_ppr(Ph);
     if (!Ph || !ranks) return GRB_NULL_POINTER;
     if (!P) return GRB_UNINITIALIZED_OBJECT;
+    if (P->broken) return GRB_INVALID_OBJECT;
     if (slot < 0 || slot >= P->slots) return GRB_INVALID_VALUE;
     Ctx* c = P->c;
     float* dst = ranks;
