@@ -795,7 +795,34 @@ static grb_info exec_pr_group(Ctx* c, const Closure& C, Group& g) {
     grb_info st;
     if ((st = ensure_plan(c, A))) return st;
     PrParams p = plan_params(c, A);
-    if (g.W) {
+    DevBuf wtmp;   // the quotient t ./ d, when it is computed once per vertex
+    if (g.W && A->nnz >= 2 * A->nrows) {
+        // Cost rule: fused into the gather, the division runs once per
+        // nonzero with two random gathers (t and d); with two or more
+        // nonzeros per row it is cheaper to compute w = t ./ d once per
+        // vertex in a streaming pass and gather w alone.  The quotients are
+        // the same values either way (rounded to the rank type).
+        wtmp = buf_alloc(c, type_size(T) * (size_t)A->ncols);
+        if (!wtmp.p) return GRB_OUT_OF_MEMORY;
+        EwSpec e;
+        e.kind = EW_EMULT;
+        e.op.code = GRB_DIV;
+        e.ctype = T;
+        e.u = vin_of(g.W->u);
+        e.v = vin_of(g.W->v);
+        WriteSpec wr;
+        VOut o;
+        o.vals = wtmp.p;
+        o.type = T;
+        o.full = 1;
+        c->stats.kernel_launches++;
+        if ((st = cuda_check(c, launch_ewise(c->stream, A->ncols, e, wr, o), "gather values"))) {
+            buf_free(c, wtmp);
+            return st;
+        }
+        p.gmode = G_W;
+        p.w = wtmp.p;
+    } else if (g.W) {
         p.gmode = G_TD;
         p.t = g.W->u->vals.p;
         p.d = g.W->v->vals.p;
@@ -811,7 +838,10 @@ static grb_info exec_pr_group(Ctx* c, const Closure& C, Group& g) {
     Node* core_root = g.E ? g.E : M;
     Version* R = core_root->out;
     const bool full = node_out_full(core_root);
-    if ((st = alloc_vec(c, R, full))) return st;
+    if ((st = alloc_vec(c, R, full))) {
+        buf_free(c, wtmp);
+        return st;
+    }
     p.out.vals = R->vals.p;
     p.out.present = (uint8_t*)R->present.p;
     p.out.type = T;
@@ -820,14 +850,19 @@ static grb_info exec_pr_group(Ctx* c, const Closure& C, Group& g) {
         p.want_resid = 1;
         const Version* ref = (g.X->v == R) ? g.X->u : g.X->v;
         p.r_old = ref->vals.p;
-        if ((st = alloc_slot(c, g.Q->out))) return st;
+        if ((st = alloc_slot(c, g.Q->out))) {
+            buf_free(c, wtmp);
+            return st;
+        }
         p.resid_slot = (double*)g.Q->out->slot.p;
         p.resid_type = g.Q->out->type;
     }
     c->stats.kernel_launches++;
     if (g.nodes.size() > 1) c->stats.fused_groups++;
     else c->stats.unfused_nodes++;
-    return cuda_check(c, launch_pr(c->stream, p, T, T, pr_grid(c, A, T, T, p.gmode, 0), 0), "fused pagerank step");
+    st = cuda_check(c, launch_pr(c->stream, p, T, T, pr_grid(c, A, T, T, p.gmode, 0), 0), "fused pagerank step");
+    buf_free(c, wtmp);   // stream-ordered: a later allocation reuses it after this kernel
+    return st;
 }
 
 // ----------------------------------------------------------- materialize
