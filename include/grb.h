@@ -133,7 +133,7 @@ typedef enum {
     GRB_OPT_HOT_BYTES = 7,     /* bytes of shared memory per SM that the persistent
                                   FP32 loop on a degree-ordered matrix uses for a
                                   copy of the most-gathered rank entries
-                                  (0 .. GRB_HOT_BYTES_MAX; default 131072; 0 = off) */
+                                  (0 .. GRB_HOT_BYTES_MAX; default 163840; 0 = off) */
     GRB_OPT_TMA_STAGES = 8     /* that loop's tile arrays: 0 (default) = register
                                   prefetch one tile ahead; 2 or 3 = bulk copies
                                   (cp.async.bulk) into shared-memory stages that

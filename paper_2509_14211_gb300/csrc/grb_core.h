@@ -182,7 +182,7 @@ struct Ctx {
     double mixed_switch = 1e-3;
     bool mixed = false;
     bool relabel = true;  // device loops run on the degree-ordered copy of the matrix
-    int64_t hot_bytes = 128 * 1024;  // shared-memory copy of the hottest gathered entries
+    int64_t hot_bytes = 160 * 1024;  // shared-memory copy of the hottest gathered entries
     int32_t tma_stages = 0;          // bulk-copy staging depth of the hot loop (0: register prefetch)
     bool dry = false;     // replaying a loop body to inspect its DAG: never execute
     DevBuf red_scratch;   // per-block partials of the reduction kernels

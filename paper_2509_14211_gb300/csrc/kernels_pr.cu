@@ -294,10 +294,13 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
 template <class T, class G, int GMODE, bool NC, bool HOT = false>
 __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int j) {
     if constexpr (HOT) {
-        // one generic load from shared memory (hot copy) or global memory,
-        // chosen per lane without a branch
-        const G* src = j < io.hot_n ? io.hot + j : io.w + j;
-        return (T)*src;
+        // the hot copy in shared memory, or L2 (bypassing L1: the columns
+        // past the copy are rarely reused soon enough for L1 to help); two
+        // predicated loads, no branch
+        float a = 0.f, b = 0.f;
+        if (j < io.hot_n) a = io.hot[j];
+        else b = __ldcg(io.w + j);
+        return (T)(a + b);
     }
     if (GMODE == G_W) {
         if (io.phase32) return (T)gload_f<float, NC>(io.w32, j);
