@@ -344,7 +344,9 @@ grb_info grb_ppr_tune(grb_ppr P, int64_t trial_bodies, double* ms_per_body, int3
 grb_info grb_ppr_layout(grb_ppr P, int32_t vw);
 
 /* Start a query in `slot` (replacing whatever it held): seeds are host
- * vertex ids (nseeds >= 1; copied), tol and itermax its loop test.
+ * vertex ids (nseeds >= 1; copied), tol and itermax its loop test.  The
+ * query is queued on the host; every queued query is placed on the device
+ * in one pass at the next grb_ppr_run / status / get / clear.
  * Errors: GRB_INVALID_VALUE (slot, nseeds or itermax out of range),
  * GRB_INVALID_INDEX (a seed outside [0, n)). */
 grb_info grb_ppr_set(grb_ppr P, int32_t slot, const int32_t* seeds, int64_t nseeds, double tol, int64_t itermax);

@@ -365,25 +365,38 @@ struct PprFinish {
     int64_t n = 0;
 };
 
-struct PprInit {
-    int32_t slot = 0, nseeds = 0, nrows = 0;
+// Admission of queued queries into their slots, all in one pass: zero each
+// slot's column of the current rank / gather buffers, place its start vector
+// (1/|S| on its seeds), its first dangling-mass term and its loop state.
+struct PprInitBatch {
+    int32_t np = 0, nrows = 0;
     int32_t width = PPR_LANES;          // slots per k-tile (32 vw)
-    const int32_t* seeds = nullptr;     // device, deduplicated
-    float r0 = 0.f;                     // 1 / nseeds
-    float* r = nullptr;                 // current rank buffer [kt][n][32]
+    int32_t cur = 0;                    // current rank buffer (recorded as the slot's last)
+    const int32_t* slots = nullptr;     // np, ascending
+    const int32_t* seed_off = nullptr;  // np + 1
+    const int32_t* seeds = nullptr;     // deduplicated seeds of every queued slot
+    const float* r0 = nullptr;          // np: 1 / |S|
+    const int32_t* act = nullptr;       // np: loop test before the first body
+    const int32_t* itermax = nullptr;   // np
+    const double* tol = nullptr;        // np
+    float* r = nullptr;                 // current rank buffer [kt][n][width]
     float* w = nullptr;
     const float* dd = nullptr;
     const uint32_t* sinkbits = nullptr;
+    int32_t* active = nullptr;          // slot state
+    int32_t* iters = nullptr;
+    int32_t* itermax_out = nullptr;
+    double* tol_out = nullptr;
+    double* resid = nullptr;
     float* tele_base = nullptr;
+    int32_t* final_buf = nullptr;
     double damping = 0.85;
 };
 
 cudaError_t launch_ppr_tiles(cudaStream_t st, const PprParams& p, int grid);
 cudaError_t launch_ppr_fixups(cudaStream_t st, const PprParams& p, int grid);
 cudaError_t launch_ppr_finish(cudaStream_t st, const PprFinish& f);
-// Zero a slot's column of r and w, then place its start vector (1/nseeds at
-// each seed) and its first dangling-mass term.
-cudaError_t launch_ppr_init_slot(cudaStream_t st, const PprInit& a);
+cudaError_t launch_ppr_init_batch(cudaStream_t st, const PprInitBatch& a);
 // Bits of every seed vertex (bits cleared first; nbits words of 32).
 cudaError_t launch_ppr_seedbits(cudaStream_t st, int32_t nseeds, const int32_t* rows, uint32_t* bits, int64_t nwords);
 // out[i] = r[kt][i][slot within the k-tile] of one slot.

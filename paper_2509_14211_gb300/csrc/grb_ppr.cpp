@@ -36,6 +36,15 @@ struct Ppr {
     int64_t exec_iters = 0;
     int exec_cur = -1;
     grb_info broken = GRB_SUCCESS;    // a failed re-layout: every later call returns it
+    // queries set since the last flush: admitted together before the next
+    // run / status / get
+    struct Pending {
+        int32_t slot;
+        std::vector<int32_t> seeds;
+        double tol;
+        int32_t itermax;
+    };
+    std::vector<Pending> pending;
 };
 
 namespace {
@@ -182,6 +191,7 @@ grb_info alloc_layout(Ppr* P, int32_t vw) {
     P->kt = (P->requested + width - 1) / width;
     P->slots = P->kt * width;
     P->seeds.assign(P->slots, {});
+    P->pending.clear();
     P->cur = 0;
     P->dirty = true;
     P->grid = ppr_blocks_per_sm(vw) * c->sm_count;
@@ -211,6 +221,82 @@ grb_info alloc_layout(Ppr* P, int32_t vw) {
         if (!st) st = cuda_check(c, cudaMemsetAsync(b->p, 0, b->bytes, c->stream), "ppr layout");
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr layout");
     P->broken = st;
+    return st;
+}
+
+// Admit every queued query: one upload of the queue, one kernel that clears
+// the queued slots' columns (adjacent slots share cache lines) and one that
+// places their start vectors and loop state.
+grb_info flush_pending(Ppr* P) {
+    if (P->pending.empty()) return GRB_SUCCESS;
+    Ctx* c = P->c;
+    std::sort(P->pending.begin(), P->pending.end(),
+              [](const Ppr::Pending& a, const Ppr::Pending& b) { return a.slot < b.slot; });
+    const int32_t np = (int32_t)P->pending.size();
+    std::vector<int32_t> slots(np), off(np + 1, 0), act(np), im(np), seeds;
+    std::vector<float> r0(np);
+    std::vector<double> tol(np);
+    for (int32_t k = 0; k < np; ++k) {
+        const auto& q = P->pending[k];
+        slots[k] = q.slot;
+        off[k + 1] = off[k] + (int32_t)q.seeds.size();
+        seeds.insert(seeds.end(), q.seeds.begin(), q.seeds.end());
+        r0[k] = (float)(1.0 / (double)q.seeds.size());
+        act[k] = (q.itermax > 0 && 1.0 > q.tol) ? 1 : 0;   // the loop test before the first body
+        im[k] = q.itermax;
+        tol[k] = q.tol;
+    }
+    // one staging buffer: doubles first, then the 4-byte arrays
+    const size_t b_tol = 8 * (size_t)np, b_i = 4 * (size_t)np;
+    const size_t bytes = b_tol + b_i * 4 + 4 * (size_t)(np + 1) + 4 * seeds.size();
+    std::vector<char> host(bytes);
+    char* h = host.data();
+    size_t o = 0;
+    auto put = [&](const void* src, size_t n) {
+        std::memcpy(h + o, src, n);
+        const size_t at = o;
+        o += n;
+        return at;
+    };
+    const size_t o_tol = put(tol.data(), b_tol), o_slots = put(slots.data(), b_i), o_r0 = put(r0.data(), b_i),
+                 o_act = put(act.data(), b_i), o_im = put(im.data(), b_i),
+                 o_off = put(off.data(), 4 * (size_t)(np + 1)), o_seeds = put(seeds.data(), 4 * seeds.size());
+    DevBuf stage = buf_alloc(c, bytes);
+    if (!stage.p) return GRB_OUT_OF_MEMORY;
+    char* d = (char*)stage.p;
+    grb_info st = cuda_check(c, cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream), "queued queries");
+    PprInitBatch a;
+    a.np = np;
+    a.nrows = (int32_t)P->n;
+    a.width = PPR_LANES * P->vw;
+    a.cur = P->cur;
+    a.slots = (const int32_t*)(d + o_slots);
+    a.seed_off = (const int32_t*)(d + o_off);
+    a.seeds = (const int32_t*)(d + o_seeds);
+    a.r0 = (const float*)(d + o_r0);
+    a.act = (const int32_t*)(d + o_act);
+    a.itermax = (const int32_t*)(d + o_im);
+    a.tol = (const double*)(d + o_tol);
+    a.r = (float*)P->r[P->cur].p;
+    a.w = (float*)P->w[P->cur].p;
+    a.dd = (const float*)P->dd.p;
+    a.sinkbits = (const uint32_t*)P->sinkbits.p;
+    a.active = (int32_t*)P->active.p;
+    a.iters = (int32_t*)P->iters.p;
+    a.itermax_out = (int32_t*)P->itermax.p;
+    a.tol_out = (double*)P->tol.p;
+    a.resid = (double*)P->resid.p;
+    a.tele_base = (float*)P->tele.p;
+    a.final_buf = (int32_t*)P->final_buf.p;
+    a.damping = P->damping;
+    if (!st) {
+        c->stats.kernel_launches += 2;
+        st = cuda_check(c, launch_ppr_init_batch(c->stream, a), "admit queries");
+    }
+    // the host staging copy must outlive the upload
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "admit queries");
+    buf_free(c, stage);
+    if (!st) P->pending.clear();
     return st;
 }
 
@@ -351,42 +437,12 @@ grb_info grb_ppr_set(grb_ppr Ph, int32_t slot, const int32_t* seeds, int64_t nse
         if (v < 0 || v >= P->n) return GRB_INVALID_INDEX;
     std::sort(S.begin(), S.end());
     S.erase(std::unique(S.begin(), S.end()), S.end());
-    Ctx* c = P->c;
-    DevBuf ds = buf_alloc(c, sizeof(int32_t) * S.size());
-    if (!ds.p) return GRB_OUT_OF_MEMORY;
-    grb_info st = cuda_check(c, cudaMemcpyAsync(ds.p, S.data(), sizeof(int32_t) * S.size(), cudaMemcpyHostToDevice,
-                                                c->stream), "seeds");
-    PprInit a;
-    a.slot = slot;
-    a.width = PPR_LANES * P->vw;
-    a.nseeds = (int32_t)S.size();
-    a.nrows = (int32_t)P->n;
-    a.seeds = (const int32_t*)ds.p;
-    a.r0 = (float)(1.0 / (double)S.size());
-    a.r = (float*)P->r[P->cur].p;
-    a.w = (float*)P->w[P->cur].p;
-    a.dd = (const float*)P->dd.p;
-    a.sinkbits = (const uint32_t*)P->sinkbits.p;
-    a.tele_base = (float*)P->tele.p;
-    a.damping = P->damping;
-    if (!st) {
-        c->stats.kernel_launches += 2;
-        st = cuda_check(c, launch_ppr_init_slot(c->stream, a), "ppr slot init");
-    }
-    // the loop test before the first body: rdiff = 1 > tol
-    const int32_t act = (itermax > 0 && 1.0 > tol) ? 1 : 0, zero = 0, im = (int32_t)itermax, fb = P->cur;
-    const double one = 1.0;
-    struct { DevBuf* b; const void* v; size_t sz; } w[] = {
-        {&P->active, &act, 4}, {&P->iters, &zero, 4}, {&P->itermax, &im, 4}, {&P->tol, &tol, 8}, {&P->resid, &one, 8},
-        {&P->final_buf, &fb, 4}};
-    for (auto& x : w)
-        if (!st)
-            st = cuda_check(c, cudaMemcpyAsync((char*)x.b->p + x.sz * slot, x.v, x.sz, cudaMemcpyHostToDevice,
-                                               c->stream), "slot state");
-    // host values above must outlive the copies
-    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "slot state");
-    buf_free(c, ds);
-    if (st) return st;
+    // queued: the slot is (re)started at the next flush, with every other
+    // query queued by then (one pass for all of them)
+    P->pending.erase(std::remove_if(P->pending.begin(), P->pending.end(),
+                                    [slot](const Ppr::Pending& q) { return q.slot == slot; }),
+                     P->pending.end());
+    P->pending.push_back({slot, S, tol, (int32_t)itermax});
     P->seeds[slot] = std::move(S);
     P->dirty = true;
     return GRB_SUCCESS;
@@ -398,9 +454,11 @@ grb_info grb_ppr_clear(grb_ppr Ph, int32_t slot) {
     if (!P) return GRB_UNINITIALIZED_OBJECT;
     if (P->broken) return GRB_INVALID_OBJECT;
     if (slot < 0 || slot >= P->slots) return GRB_INVALID_VALUE;
+    grb_info st = flush_pending(P);
+    if (st) return st;
     const int32_t zero = 0;
-    grb_info st = cuda_check(P->c, cudaMemcpyAsync((int32_t*)P->active.p + slot, &zero, 4, cudaMemcpyHostToDevice,
-                                                   P->c->stream), "slot clear");
+    st = cuda_check(P->c, cudaMemcpyAsync((int32_t*)P->active.p + slot, &zero, 4, cudaMemcpyHostToDevice,
+                                          P->c->stream), "slot clear");
     if (!st) st = cuda_check(P->c, cudaStreamSynchronize(P->c->stream), "slot clear");
     if (st) return st;
     P->seeds[slot].clear();
@@ -417,8 +475,8 @@ grb_info grb_ppr_run(grb_ppr Ph, int64_t iters) {
     if (iters < 0 || iters > 100000) return GRB_INVALID_VALUE;
     if (iters == 0) return GRB_SUCCESS;
     Ctx* c = P->c;
-    grb_info st = GRB_SUCCESS;
-    if (P->dirty) st = upload_seeds(P);
+    grb_info st = flush_pending(P);
+    if (!st && P->dirty) st = upload_seeds(P);
     if (st) return st;
     if (!P->exec || P->exec_iters != iters || P->exec_cur != P->cur) {
         drop_graph(P);
@@ -451,6 +509,8 @@ grb_info grb_ppr_status(grb_ppr Ph, int32_t* active, int64_t* iters, double* res
     if (!P) return GRB_UNINITIALIZED_OBJECT;
     if (P->broken) return GRB_INVALID_OBJECT;
     Ctx* c = P->c;
+    grb_info st0 = flush_pending(P);
+    if (st0) return st0;
     const int S = P->slots;
     std::vector<int32_t> a(S), it(S);
     std::vector<double> rs(S);
@@ -477,6 +537,8 @@ grb_info grb_ppr_get(grb_ppr Ph, int32_t slot, float* ranks, int out_is_device) 
     if (P->broken) return GRB_INVALID_OBJECT;
     if (slot < 0 || slot >= P->slots) return GRB_INVALID_VALUE;
     Ctx* c = P->c;
+    grb_info st0 = flush_pending(P);
+    if (st0) return st0;
     float* dst = ranks;
     DevBuf tmp;
     if (!out_is_device) {

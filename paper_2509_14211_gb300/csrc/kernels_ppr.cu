@@ -395,29 +395,45 @@ __global__ void ppr_finish_kernel(const __grid_constant__ PprFinish f) {
     }
 }
 
-__global__ void ppr_init_zero_kernel(PprInit a) {
-    const int kt = a.slot / a.width, l = a.slot % a.width;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nrows; i += gridDim.x * blockDim.x) {
-        const size_t o = ((size_t)kt * a.nrows + i) * a.width + l;
+// Queued slots of one row are adjacent threads, so their zero writes share
+// the row's cache lines.
+__global__ void ppr_init_zero_kernel(const __grid_constant__ PprInitBatch a) {
+    const int64_t total = (int64_t)a.nrows * a.np;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / a.np;
+        const int s = a.slots[q - i * a.np];
+        const int kt = s / a.width, l = s % a.width;
+        const size_t o = ((size_t)kt * a.nrows + (size_t)i) * a.width + l;
         a.r[o] = 0.f;
         a.w[o] = 0.f;
     }
 }
 
-__global__ void ppr_init_seed_kernel(PprInit a) {
-    const int kt = a.slot / a.width, l = a.slot % a.width;
-    for (int q = threadIdx.x; q < a.nseeds; q += blockDim.x) {
+// One CTA per queued slot: its seeds, its first teleport term and its state.
+__global__ void ppr_init_seed_kernel(const __grid_constant__ PprInitBatch a) {
+    const int k = blockIdx.x;
+    const int s = a.slots[k];
+    const int kt = s / a.width, l = s % a.width;
+    const int b = a.seed_off[k], e = a.seed_off[k + 1];
+    const float r0 = a.r0[k];
+    for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
         const int i = a.seeds[q];
         const size_t o = ((size_t)kt * a.nrows + i) * a.width + l;
-        a.r[o] = a.r0;
-        a.w[o] = a.r0 / a.dd[i];
+        a.r[o] = r0;
+        a.w[o] = r0 / a.dd[i];
     }
-    // dangling mass of the start vector (one thread, in seed order)
     if (threadIdx.x == 0) {
+        // dangling mass of the start vector, in seed order
         double D = 0.0;
-        for (int q = 0; q < a.nseeds; ++q)
-            if ((a.sinkbits[a.seeds[q] >> 5] >> (a.seeds[q] & 31)) & 1u) D += (double)a.r0;
-        a.tele_base[a.slot] = (float)(a.damping * D / (double)a.nrows);
+        for (int q = b; q < e; ++q)
+            if ((a.sinkbits[a.seeds[q] >> 5] >> (a.seeds[q] & 31)) & 1u) D += (double)r0;
+        a.tele_base[s] = (float)(a.damping * D / (double)a.nrows);
+        a.active[s] = a.act[k];
+        a.iters[s] = 0;
+        a.itermax_out[s] = a.itermax[k];
+        a.tol_out[s] = a.tol[k];
+        a.resid[s] = 1.0;
+        a.final_buf[s] = a.cur;
     }
 }
 
@@ -500,11 +516,12 @@ cudaError_t launch_ppr_finish(cudaStream_t st, const PprFinish& f) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_ppr_init_slot(cudaStream_t st, const PprInit& a) {
-    ppr_init_zero_kernel<<<grid_1d(a.nrows), 256, 0, st>>>(a);
+cudaError_t launch_ppr_init_batch(cudaStream_t st, const PprInitBatch& a) {
+    if (a.np <= 0) return cudaSuccess;
+    ppr_init_zero_kernel<<<grid_1d((int64_t)a.nrows * a.np), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ppr_init_seed_kernel<<<1, 256, 0, st>>>(a);
+    ppr_init_seed_kernel<<<a.np, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
