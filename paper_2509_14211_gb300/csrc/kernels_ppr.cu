@@ -260,7 +260,9 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
             Vec<V> g[U];
 #pragma unroll
             for (int q = 0; q < U; ++q) {
-                if (src * PR_NZLANE + q0 + q < nvalid) {
+                // lanes whose slots are all finished or empty load nothing
+                // (in a partly filled k-tile the line traffic shrinks)
+                if (L.any && src * PR_NZLANE + q0 + q < nvalid) {
                     g[q].ld(Wb + (size_t)c[q0 + q] * W);
                 } else {
 #pragma unroll
