@@ -427,11 +427,11 @@ int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int 
 // Dynamic shared memory of the hot persistent kernel.
 size_t pr_hot_dynamic_smem(int32_t hot_n, int32_t tma_stages);
 // Static shared memory of the hot persistent kernel (bytes, upper bound).
-constexpr size_t PR_HOT_STATIC_SMEM = 34 * 1024;
+constexpr size_t PR_HOT_STATIC_SMEM = 26 * 1024;
 constexpr size_t PR_SMEM_PER_BLOCK_MAX = 227 * 1024;
 // Threads per CTA of the persistent kernel with the shared-memory hot copy
 // (one CTA per SM).
-constexpr int PR_HOT_BLOCK = 1024;
+constexpr int PR_HOT_BLOCK = 768;
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,
                       int persistent);
 cudaError_t launch_barrier_selftest(cudaStream_t st, SyncWords* sync, int32_t* status, int64_t spin_limit, int grid);

@@ -298,8 +298,8 @@ __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, i
         // past the copy are rarely reused soon enough for L1 to help); two
         // predicated loads, no branch
         float a = 0.f, b = 0.f;
-        if (j < io.hot_n) a = io.hot[j];
-        else b = __ldcg(io.w + j);
+        if (j < io.hot_n) a = (float)io.hot[j];
+        else b = (float)__ldcg(io.w + j);
         return (T)(a + b);
     }
     if (GMODE == G_W) {
@@ -348,37 +348,52 @@ __device__ __forceinline__ TilePre tile_pre(const PrParams& p, int t, uint32_t m
     return f;
 }
 
+// What a tile's loads deliver: the gathered values of the lane's nonzeros
+// and the epilogue inputs of the first row the lane finishes.
+template <class T>
+struct TileVals {
+    T v[PR_NZLANE];
+    RowIn<T> pre;
+};
+
+// First half of a tile: issue its gathers and the epilogue loads of the
+// lane's first row.  Nothing waits for them here.
 template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false>
-__device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io,
-                                          Acc<T>& resid, Acc<T>& dang, WarpSmem<T>& ws) {
+__device__ __forceinline__ TileVals<T> tile_issue(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io) {
     static_assert(PR_NZLANE == 8, "two 16-byte column loads per lane");
     const int lane = threadIdx.x & 31;
-    const uint32_t meta = f.meta;
-    const int rfirst = (int)(meta & 0x7fffffffu);
-    const int x_lo = (int)(meta >> 31);
     const int kl = t * PR_NZTILE + lane * PR_NZLANE;
-    const int4 ca = f.ca, cb = f.cb;
-    const uint32_t myf = (f.bits >> (kl & 31)) & 0xffu;
     const int nvalid = min(max(p.nnz - kl, 0), PR_NZLANE);
-    int pre_i = 0;
-    RowIn<T> pre;
-    pre.rold = (T)0;
-    pre.dd = (T)1;
-    pre.sinkword = 0;
-    if (f.pre_i >= 0) {
-        pre_i = f.pre_i;
-        pre = row_inputs<T, G, NC, EPI>(p, io, pre_i);
-    }
-    const int cols[PR_NZLANE] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-    T v[PR_NZLANE];
+    TileVals<T> tv;
+    tv.pre.rold = (T)0;
+    tv.pre.dd = (T)1;
+    tv.pre.sinkword = 0;
+    if (f.pre_i >= 0) tv.pre = row_inputs<T, G, NC, EPI>(p, io, f.pre_i);
+    const int cols[PR_NZLANE] = {f.ca.x, f.ca.y, f.ca.z, f.ca.w, f.cb.x, f.cb.y, f.cb.z, f.cb.w};
 #pragma unroll
     for (int q = 0; q < PR_NZLANE; ++q) {
         // padding entries of the last tile hold column 0: the load is in
         // bounds, and its value is discarded
         const T g = gather<T, G, GMODE, NC, HOT>(p, io, cols[q]);
-        v[q] = q < nvalid ? g : (T)0;
+        tv.v[q] = q < nvalid ? g : (T)0;
     }
+    return tv;
+}
 
+// Second half: row numbering, segmented sums, carries and the epilogue.
+template <class T, class G, bool NC, int EPI>
+__device__ __forceinline__ void tile_finish(const PrParams& p, int t, const TilePre& f, const TileVals<T>& tv,
+                                            const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                            WarpSmem<T>& ws) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t meta = f.meta;
+    const int rfirst = (int)(meta & 0x7fffffffu);
+    const int x_lo = (int)(meta >> 31);
+    const int kl = t * PR_NZTILE + lane * PR_NZLANE;
+    const uint32_t myf = (f.bits >> (kl & 31)) & 0xffu;
+    const int pre_i = f.pre_i >= 0 ? f.pre_i : 0;
+    const RowIn<T>& pre = tv.pre;
+    const T* v = tv.v;
     // ---- row numbering: rows ending before this lane's nonzeros
     const int cnt = __popc(myf);
     int incl = cnt;
@@ -427,6 +442,13 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePr
         row_epilogue<T, G, EPI>(p, io, i, ws.rowsum[x], true, in, resid, dang);
     }
     __syncwarp();
+}
+
+template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false>
+__device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io,
+                                          Acc<T>& resid, Acc<T>& dang, WarpSmem<T>& ws) {
+    const TileVals<T> tv = tile_issue<T, G, GMODE, NC, EPI, HOT>(p, t, f, io);
+    tile_finish<T, G, NC, EPI>(p, t, f, tv, io, resid, dang, ws);
 }
 
 // Rows without nonzeros: the epilogue with an empty sum.
@@ -499,6 +521,43 @@ __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& i
         warp_tile<T, G, GMODE, NC, EPI, HOT>(p, t, cur, io, resid, dang, sm.w[warp]);
     }
     empty_rows<T, G, NC, EPI>(p, io, resid, dang);
+}
+
+// Phase A with the gathers one tile deep: tile t+nwarps's gathers are issued
+// before tile t's scans and epilogue, so every warp keeps two tiles' loads in
+// flight; tile-start loads run two tiles ahead and the metadata three.
+template <class T, class G, int GMODE, int EPI, bool HOT, int NW>
+__device__ __forceinline__ void phase_a_pipe(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                             Smem<T, NW>& sm) {
+    const int warp = threadIdx.x >> 5;
+    const int nw = gridDim.x * NW;
+    int t = blockIdx.x * NW + warp;
+    if (t < p.ntiles) {
+        TilePre f0 = tile_pre(p, t, __ldg(p.tile_meta + t));
+        TilePre f1;
+        f1.pre_i = -1;
+        f1.meta = 0u;
+        if (t + nw < p.ntiles) f1 = tile_pre(p, t + nw, __ldg(p.tile_meta + t + nw));
+        uint32_t meta2 = t + 2 * nw < p.ntiles ? __ldg(p.tile_meta + t + 2 * nw) : 0u;
+        TileVals<T> v0 = tile_issue<T, G, GMODE, false, EPI, HOT>(p, t, f0, io);
+        for (; t < p.ntiles; t += nw) {
+            const int t1 = t + nw, t2 = t + 2 * nw, t3 = t + 3 * nw;
+            TileVals<T> v1;
+            if (t1 < p.ntiles) v1 = tile_issue<T, G, GMODE, false, EPI, HOT>(p, t1, f1, io);
+            TilePre f2;
+            f2.pre_i = -1;
+            f2.meta = 0u;
+            if (t2 < p.ntiles) {
+                f2 = tile_pre(p, t2, meta2);
+                meta2 = t3 < p.ntiles ? __ldg(p.tile_meta + t3) : 0u;
+            }
+            tile_finish<T, G, false, EPI>(p, t, f0, v0, io, resid, dang, sm.w[warp]);
+            f0 = f1;
+            f1 = f2;
+            v0 = v1;
+        }
+    }
+    empty_rows<T, G, false, EPI>(p, io, resid, dang);
 }
 
 // ------------------------------------------------ bulk-copy staging of tiles
@@ -701,8 +760,10 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 // are the most-gathered entries (for R-MAT, the first 32K of 4M vertices
 // take about half of all gathers), so half of the random gathers never reach
 // L1/L2; the copy costs hot_n words per CTA per body from L2.
+static_assert(sizeof(Smem<float, PR_HOT_BLOCK / 32>) <= PR_HOT_STATIC_SMEM, "static shared memory bound");
+
 template <class T, class G, int BLK, bool HOT, int NST = 0>
-__global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
+__global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS))
     pr_persistent_kernel(const __grid_constant__ PrParams p) {
     __shared__ Smem<T, BLK / 32> sm;
     extern __shared__ int4 hot_raw[];
@@ -767,6 +828,8 @@ __global__ void __launch_bounds__(BLK, (BLK >= 1024 ? 1 : PR_MINBLOCKS))
         Acc<T> racc, dacc;
         if constexpr (NST > 0)
             phase_a_tma<T, G, G_W, EPI_LEAN, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
+        else if constexpr (HOT)
+            phase_a_pipe<T, G, G_W, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
         else
             phase_a<T, G, G_W, false, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
