@@ -683,7 +683,7 @@ def main():
     kernel_ms = sum(kernel_ns) / len(kernel_ns) / 1e6
     achieved = launch_bytes / (kernel_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _traffic_per_launch(), "peak_source": peak_kind, "kernel": "pr_persistent_kernel<float,float,1024,1> (degree-ordered matrix, shared-memory hot copy)",
+                "traffic": _traffic_per_launch(), "peak_source": peak_kind, "kernel": "pr_persistent_kernel<float,float,768,1,0> (degree-ordered matrix, shared-memory hot copy, gathers one tile deep)",
                 "kernel_ms_per_launch": kernel_ms, "algorithmic_bytes_per_launch": launch_bytes}
 
     out = {

@@ -452,13 +452,34 @@ __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePr
 }
 
 // Rows without nonzeros: the epilogue with an empty sum.
-template <class T, class G, bool NC, int EPI>
+// U rows per step: their index loads, then their input loads, are issued
+// together (one round trip each instead of one per row); a thread still
+// takes its rows in grid-stride order, so U does not change the sums.
+template <class T, class G, bool NC, int EPI, int U = 1>
 __device__ __forceinline__ void empty_rows(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang) {
     const int nthreads = gridDim.x * blockDim.x;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.n_empty; e += nthreads) {
-        const int i = ld_stream(p.empty_rows + e);
-        const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, i);
-        row_epilogue<T, G, EPI>(p, io, i, (T)0, false, in, resid, dang);
+    if constexpr (U == 1) {
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.n_empty; e += nthreads) {
+            const int i = ld_stream(p.empty_rows + e);
+            const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, i);
+            row_epilogue<T, G, EPI>(p, io, i, (T)0, false, in, resid, dang);
+        }
+        return;
+    }
+    for (int e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < p.n_empty; e0 += U * nthreads) {
+        int i[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nthreads;
+            i[u] = e < p.n_empty ? ld_stream(p.empty_rows + e) : -1;
+        }
+        RowIn<T> in[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i[u] >= 0) in[u] = row_inputs<T, G, NC, EPI>(p, io, i[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i[u] >= 0) row_epilogue<T, G, EPI>(p, io, i[u], (T)0, false, in[u], resid, dang);
     }
 }
 
@@ -557,7 +578,7 @@ __device__ __forceinline__ void phase_a_pipe(const PrParams& p, const TileIO<T, 
             v0 = v1;
         }
     }
-    empty_rows<T, G, false, EPI>(p, io, resid, dang);
+    empty_rows<T, G, false, EPI, 4>(p, io, resid, dang);
 }
 
 // ------------------------------------------------ bulk-copy staging of tiles
