@@ -224,7 +224,7 @@ __device__ __forceinline__ void zero_smem(PprSmem& sm) {
 // slots' values of each source vertex.  Loads are issued U nonzeros at a
 // time (U V floats per lane in flight).
 template <int V>
-__device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int lane, Lane<V>& L) {
+__device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int lane, Lane<V>& L, bool all_live) {
     constexpr int U = V == 4 ? 4 : 8;
     constexpr int W = PPR_LANES * V;
     const uint32_t meta = __ldg(p.tile_meta + t);
@@ -238,6 +238,7 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
     const int pre_i = rfirst + lane < p.n_ne ? __ldg(p.ne_rows + rfirst + lane) : 0;
     const float* Wb = p.w_old + (size_t)kt * (size_t)p.nrows * W + (size_t)lane * V;
     const size_t tslot = ((size_t)kt * p.ntiles + t) * W + (size_t)lane * V;
+    const bool dense = all_live && nvalid == PR_NZTILE;
     float acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0.f;
@@ -258,22 +259,37 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
 #pragma unroll
         for (int q0 = 0; q0 < PR_NZLANE; q0 += U) {
             Vec<V> g[U];
+            if (dense) {
+                // a whole tile and every lane with a live slot: no per-load test
 #pragma unroll
-            for (int q = 0; q < U; ++q) {
-                // lanes whose slots are all finished or empty load nothing
-                // (in a partly filled k-tile the line traffic shrinks)
-                if (L.any && src * PR_NZLANE + q0 + q < nvalid) {
-                    g[q].ld(Wb + (size_t)c[q0 + q] * W);
-                } else {
+                for (int q = 0; q < U; ++q) g[q].ld(Wb + (size_t)c[q0 + q] * W);
+            } else {
 #pragma unroll
-                    for (int v = 0; v < V; ++v) g[q].x[v] = 0.f;
+                for (int q = 0; q < U; ++q) {
+                    // lanes whose slots are all finished or empty load nothing
+                    // (in a partly filled k-tile the line traffic shrinks)
+                    if (L.any && src * PR_NZLANE + q0 + q < nvalid) {
+                        g[q].ld(Wb + (size_t)c[q0 + q] * W);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) g[q].x[v] = 0.f;
+                    }
                 }
+            }
+            const uint32_t fq = (f >> q0) & ((1u << U) - 1u);
+            if (fq == 0u) {
+                // no row ends among these U nonzeros (the same in every lane)
+#pragma unroll
+                for (int q = 0; q < U; ++q)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] += g[q].x[v];
+                continue;
             }
 #pragma unroll
             for (int q = 0; q < U; ++q) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] += g[q].x[v];
-                if ((f >> (q0 + q)) & 1u) {
+                if ((fq >> q) & 1u) {
                     if (r == 0 && x_lo) {
                         Vec<V> a;
 #pragma unroll
@@ -314,7 +330,8 @@ __global__ void __launch_bounds__(PPR_BLOCK, (V == 4 ? 1 : 2)) ppr_tiles_kernel(
         // a k-tile without an active slot is skipped (the same decision in
         // every warp: all read the same flags)
         if (!__any_sync(FULL, L.any)) continue;
-        for (int t = w0; t < p.ntiles; t += nwarps) ppr_tile<V>(p, kt, t, lane, L);
+        const bool all_live = __all_sync(FULL, L.any);   // every lane has a live slot
+        for (int t = w0; t < p.ntiles; t += nwarps) ppr_tile<V>(p, kt, t, lane, L, all_live);
         // rows without nonzeros: the epilogue with an empty sum
         float zero[V];
 #pragma unroll
