@@ -194,19 +194,34 @@ __global__ void relabel_rowlen_kernel(int32_t n, const int32_t* __restrict__ row
     }
 }
 
-// Columns of the relabelled A^T, one warp per new row: the old row's
-// entries in their old order, each column renamed by old2new.
-__global__ void relabel_cols_kernel(int32_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                                    const int32_t* __restrict__ new2old, const int32_t* __restrict__ old2new,
-                                    const int32_t* __restrict__ new_ptr, int32_t* new_col) {
-    const int lane = threadIdx.x & 31;
-    const int32_t nw = gridDim.x * (blockDim.x / 32);
-    for (int32_t k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); k < n; k += nw) {
-        const int32_t o = new2old[k];
-        const int32_t b = row_ptr[o], len = row_ptr[o + 1] - b, nb = new_ptr[k];
-        for (int32_t q = lane; q < len; q += 32) new_col[nb + q] = old2new[col_idx[b + q]];
+// Columns of the relabelled A^T: each new row holds the old row's entries in
+// their old order, each column renamed by old2new.
+//
+// Row starts of the renumbered matrix: rid[new_ptr[k]] = k for every
+// non-empty row k (a max-scan then gives every nonzero its row).
+__global__ void row_start_kernel(int32_t n, const int32_t* __restrict__ new_ptr, int32_t* rid) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int32_t b = new_ptr[k];
+        if (new_ptr[k + 1] > b) rid[b] = k;
     }
 }
+
+// One thread per nonzero of the renumbered matrix: nonzero p of new row k
+// is entry p - new_ptr[k] of old row new2old[k], its column renumbered.
+__global__ void relabel_cols_flat_kernel(int64_t nnz, const int32_t* __restrict__ rid,
+                                         const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                         const int32_t* __restrict__ new2old, const int32_t* __restrict__ old2new,
+                                         const int32_t* __restrict__ new_ptr, int32_t* new_col) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = rid[p];
+        const int32_t o = new2old[k];
+        new_col[p] = old2new[col_idx[row_ptr[o] + (int32_t)(p - new_ptr[k])]];
+    }
+}
+
+struct MaxI32 {
+    __device__ __forceinline__ int32_t operator()(int32_t a, int32_t b) const { return a > b ? a : b; }
+};
 
 __global__ void permute_gather_kernel(int32_t n, const int32_t* __restrict__ perm, const void* in, void* out,
                                       int32_t esize) {
@@ -491,9 +506,23 @@ cudaError_t relabel_build(cudaStream_t st, const RelabelArgs& a, AllocFn af, Fre
     if ((e = cub::DeviceScan::ExclusiveSum(tmp, tb, deg, a.new_row_ptr, n + 1, st)) != cudaSuccess) return e;
     // padding of the last tile: column 0, as in the CSR build
     if ((e = cudaMemsetAsync(a.new_col_idx, 0, sizeof(int32_t) * padded_nnz(a.nnz), st)) != cudaSuccess) return e;
-    relabel_cols_kernel<<<grid_for((int64_t)n * 32), 256, 0, st>>>(n, a.row_ptr, a.col_idx, a.new2old, a.old2new,
-                                                                   a.new_row_ptr, a.new_col_idx);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.nnz > 0) {
+        // every nonzero's new row (row starts, then a max-scan), then one
+        // thread per nonzero: all lanes busy whatever the row lengths
+        int32_t* rid = (int32_t*)S.get(sizeof(int32_t) * (size_t)a.nnz);
+        if (!rid) return cudaErrorMemoryAllocation;
+        if ((e = cudaMemsetAsync(rid, 0, sizeof(int32_t) * (size_t)a.nnz, st)) != cudaSuccess) return e;
+        row_start_kernel<<<grid_for(n), 256, 0, st>>>(n, a.new_row_ptr, rid);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        size_t sb = 0;
+        if ((e = cub::DeviceScan::InclusiveScan(nullptr, sb, rid, rid, MaxI32(), a.nnz, st)) != cudaSuccess) return e;
+        void* stmp = S.get(sb);
+        if (!stmp) return cudaErrorMemoryAllocation;
+        if ((e = cub::DeviceScan::InclusiveScan(stmp, sb, rid, rid, MaxI32(), a.nnz, st)) != cudaSuccess) return e;
+        relabel_cols_flat_kernel<<<grid_for(a.nnz), 256, 0, st>>>(a.nnz, rid, a.row_ptr, a.col_idx, a.new2old,
+                                                                  a.old2new, a.new_row_ptr, a.new_col_idx);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return cudaStreamSynchronize(st);
 }
 
