@@ -651,8 +651,7 @@ def main():
         A2 = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, s_dev, d_dev, None, BUILD_FLAGS)
         P2 = PageRankProblem(ctx, A2, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
         P2.run(-1.0, ITERS, "device")
-        vals, _ = grb.grb_vector_extract_dense(P2.r, grb.GRB_FP32, present=False)
-        out_host.copy_(torch.from_numpy(vals))
+        grb.grb_vector_extract_dense(P2.r, grb.GRB_FP32, out=out_host, present=False)
         barrier()
         dt = time.perf_counter() - t0
         P2.free()

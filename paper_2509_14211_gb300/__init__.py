@@ -344,11 +344,22 @@ def grb_vector_nvals(v: int) -> int:
 
 def grb_vector_extract_dense(v: int, type_: int, out=None, present: bool = True):
     """Values (numpy array of the vector's type, absent -> 0) and a uint8
-    presence array.  With `out` a torch CUDA tensor the values are written to
-    the device instead and (out, None) is returned."""
+    presence array.  With `out` (a contiguous torch tensor or numpy array of
+    the vector's length and element size) the values are written there
+    instead -- straight to the device for a CUDA tensor, by one copy from the
+    device for a host buffer (pinned: at the link's full rate) -- and
+    (out, None) is returned."""
     n = grb_vector_size(v)
-    if out is not None and _is_device(out):
-        _check(load().grb_vector_extract_dense(v, _ptr(out), None, 1), "grb_vector_extract_dense", v)
+    if out is not None:
+        esize = out.element_size() if hasattr(out, "element_size") else out.itemsize
+        contiguous = out.is_contiguous() if hasattr(out, "is_contiguous") else out.flags["C_CONTIGUOUS"]
+        count = out.numel() if hasattr(out, "numel") else out.size
+        if count != n:
+            raise ValueError("out must hold one element per vector entry")
+        if esize != np.dtype(NP_TYPES[type_]).itemsize or not contiguous:
+            raise ValueError("out must be contiguous with the vector type's element size")
+        dev = 1 if _is_device(out) else 0
+        _check(load().grb_vector_extract_dense(v, _ptr(out), None, dev), "grb_vector_extract_dense", v)
         return out, None
     vals = np.empty(n, dtype=NP_TYPES[type_])
     pres = np.empty(n, dtype=np.uint8) if present else None

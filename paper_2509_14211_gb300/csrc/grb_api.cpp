@@ -415,10 +415,16 @@ grb_info grb_matrix_col_degree(grb_vector deg, grb_matrix Am) {
     v->vals = buf_alloc(c, sizeof(int32_t) * d->n);
     v->present = buf_alloc(c, (size_t)d->n);
     grb_info st = (v->vals.p && v->present.p) ? GRB_SUCCESS : GRB_OUT_OF_MEMORY;
+    // the column counts are computed once per matrix (the degree order of
+    // the device loops reuses them)
+    if (!st) st = ensure_coldeg(c, A);
     if (!st)
-        st = cuda_check(c, launch_col_degree(c->stream, A->ncols, A->nnz, (const int32_t*)A->col_idx.p,
-                                             (int32_t*)v->vals.p, (uint8_t*)v->present.p), "col degree");
-    c->stats.kernel_launches += 2;
+        st = cuda_check(c, cudaMemcpyAsync(v->vals.p, A->coldeg.p, sizeof(int32_t) * (size_t)A->ncols,
+                                           cudaMemcpyDeviceToDevice, c->stream), "col degree");
+    if (!st)
+        st = cuda_check(c, launch_deg_present(c->stream, A->ncols, (const int32_t*)A->coldeg.p,
+                                              (uint8_t*)v->present.p), "col degree");
+    c->stats.kernel_launches++;
     v->fmt = Fmt::BITMAP;
     v->ready = true;
     if (st) {

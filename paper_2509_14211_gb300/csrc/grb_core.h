@@ -122,6 +122,7 @@ struct Matrix {
     double iso_val = 1.0;
     int64_t nonempty_rows = -1;
     TilePlan* plan = nullptr;
+    DevBuf coldeg;             // int32[ncols] entries per column (out-degree when this is A^T), computed once
     // degree-ordered copy of a square pattern matrix for the device loops
     Matrix* rel = nullptr;
     DevBuf new2old, old2new;
@@ -240,6 +241,7 @@ grb_info cuda_check(Ctx* c, cudaError_t e, const char* what);
 grb_info ensure_plan(Ctx* c, Matrix* A);
 grb_info ensure_sinkbits(Ctx* c, Version* sinks);
 grb_info ensure_relabel(Ctx* c, Matrix* A);
+grb_info ensure_coldeg(Ctx* c, Matrix* A);
 grb_info ensure_perm_copy(Ctx* c, Matrix* A, Version* v, bool bits);
 struct Ppr;
 void ppr_destroy(Ppr* P);

@@ -208,9 +208,28 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
 static constexpr int32_t REL_TOP = 32768;
 static constexpr double REL_MIN_COVER = 0.10;
 
+grb_info ensure_coldeg(Ctx* c, Matrix* A) {
+    if (A->coldeg.p) return GRB_SUCCESS;
+    DevBuf d = buf_alloc(c, sizeof(int32_t) * (size_t)(A->ncols > 0 ? A->ncols : 1));
+    if (!d.p) return GRB_OUT_OF_MEMORY;
+    c->stats.kernel_launches++;
+    grb_info st = cuda_check(c, launch_col_count(c->stream, A->ncols, A->nnz, (const int32_t*)A->col_idx.p,
+                                                 (int32_t*)d.p), "column count");
+    if (st) {
+        buf_free(c, d);
+        return st;
+    }
+    A->coldeg = d;
+    return GRB_SUCCESS;
+}
+
 grb_info ensure_relabel(Ctx* c, Matrix* A) {
     if (A->rel || A->rel_checked) return GRB_SUCCESS;
     if (A->nrows != A->ncols || A->vals.p || A->nrows <= 0) return GRB_INVALID_VALUE;
+    {
+        const grb_info sd = ensure_coldeg(c, A);
+        if (sd) return sd;
+    }
     const int64_t n = A->nrows;
     auto af = [](void* x, size_t b) { return dev_alloc((Ctx*)x, b); };
     auto ff = [](void* x, void* q, size_t b) { dev_free((Ctx*)x, q, b); };
@@ -226,10 +245,11 @@ grb_info ensure_relabel(Ctx* c, Matrix* A) {
     a.new2old = (int32_t*)n2o.p;
     a.old2new = (int32_t*)o2n.p;
     a.top_h = REL_TOP;
+    a.coldeg = (const int32_t*)A->coldeg.p;
     unsigned long long top = 0;
     if (!st) {
         st = cuda_check(c, relabel_order(c->stream, a, &top, af, ff, c), "relabel order");
-        c->stats.kernel_launches += 6;
+        c->stats.kernel_launches += 5;
     }
     if (!st && (double)top < REL_MIN_COVER * (double)A->nnz) {
         A->rel_checked = true;

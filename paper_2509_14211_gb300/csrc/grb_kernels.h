@@ -248,6 +248,10 @@ using AllocFn = void* (*)(void* ctx, size_t bytes);
 using FreeFn = void (*)(void* ctx, void* p, size_t bytes);
 cudaError_t csr_build(cudaStream_t st, const CsrBuildArgs& a, AllocFn af, FreeFn ff, void* actx,
                       int32_t** row_ptr, int32_t** col_idx, void** vals_out, int64_t* nnz_out, int32_t* bad_index);
+// deg[j] = entries in column j
+cudaError_t launch_col_count(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx, int32_t* deg);
+// present[j] = deg[j] > 0
+cudaError_t launch_deg_present(cudaStream_t st, int64_t ncols, const int32_t* deg, uint8_t* present);
 cudaError_t launch_col_degree(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx,
                               int32_t* deg, uint8_t* present);
 cudaError_t launch_nonempty_rows(cudaStream_t st, int64_t nrows, const int32_t* row_ptr, unsigned long long* out);
@@ -293,6 +297,7 @@ struct RelabelArgs {
     int32_t* new2old;
     int32_t* old2new;
     int32_t top_h;
+    const int32_t* coldeg = nullptr;   // entries per column (relabel_order), computed by the caller
 };
 cudaError_t relabel_order(cudaStream_t st, const RelabelArgs& a, unsigned long long* top_sum, AllocFn af, FreeFn ff,
                           void* actx);

@@ -173,6 +173,7 @@ void matrix_unref(Matrix* A) {
     buf_free(c, A->row_ptr);
     buf_free(c, A->col_idx);
     buf_free(c, A->vals);
+    buf_free(c, A->coldeg);
     if (A->plan) {
         TilePlan* p = A->plan;
         buf_free(c, p->meta);

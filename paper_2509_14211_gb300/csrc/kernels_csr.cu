@@ -386,6 +386,18 @@ cudaError_t csr_build(cudaStream_t st, const CsrBuildArgs& a, AllocFn af, FreeFn
     return cudaSuccess;
 }
 
+cudaError_t launch_col_count(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx, int32_t* deg) {
+    cudaError_t e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * (ncols > 0 ? ncols : 1), st);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0) col_count_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, col_idx, deg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deg_present(cudaStream_t st, int64_t ncols, const int32_t* deg, uint8_t* present) {
+    if (ncols > 0) deg_present_kernel<<<grid_for(ncols), 256, 0, st>>>(ncols, deg, present);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_col_degree(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx, int32_t* deg,
                               uint8_t* present) {
     cudaError_t e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * (ncols > 0 ? ncols : 1), st);
@@ -480,15 +492,7 @@ cudaError_t block_degree_order(cudaStream_t st, int32_t n, const int32_t* col_id
 
 cudaError_t relabel_order(cudaStream_t st, const RelabelArgs& a, unsigned long long* top_sum, AllocFn af, FreeFn ff,
                           void* actx) {
-    Scratch S{af, ff, actx, {}};
-    cudaError_t e;
-    const int32_t n = a.n;
-    int32_t* deg = (int32_t*)S.get(sizeof(int32_t) * (n + 1));
-    if (!deg) return cudaErrorMemoryAllocation;
-    if ((e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st)) != cudaSuccess) return e;
-    if (a.nnz > 0) col_count_kernel<<<grid_for(a.nnz), 256, 0, st>>>(a.nnz, a.col_idx, deg);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return degree_order(st, n, deg, a.new2old, a.old2new, af, ff, actx, a.top_h, top_sum);
+    return degree_order(st, a.n, a.coldeg, a.new2old, a.old2new, af, ff, actx, a.top_h, top_sum);
 }
 
 cudaError_t relabel_build(cudaStream_t st, const RelabelArgs& a, AllocFn af, FreeFn ff, void* actx) {

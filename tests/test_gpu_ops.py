@@ -261,6 +261,32 @@ def test_mxv_accum_and_mask(grb, ctx):
 
 
 # ------------------------------------------------------------ API errors
+def test_extract_dense_into_caller_buffers(grb, ctx):
+    """Values land in a caller's buffer: a CUDA tensor, a pinned or pageable
+    host tensor, a numpy array -- the same values as the returned array;
+    absent entries read 0; a wrong length or element size is refused."""
+    import torch
+
+    n = 1000
+    sv = _rand_sparse(np.random.default_rng(11), n, 0.4)
+    sv = SparseVec(n, sv.idx, sv.val.astype(np.float32))
+    v = _upload(grb, ctx, sv, grb.GRB_FP32)
+    want, pres = grb.grb_vector_extract_dense(v, grb.GRB_FP32)
+    assert np.array_equal(np.nonzero(pres)[0], sv.idx) and np.all(want[pres == 0] == 0)
+    outs = [torch.empty(n, dtype=torch.float32, device="cuda"), torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.float32), np.empty(n, dtype=np.float32)]
+    for out in outs:
+        got, none = grb.grb_vector_extract_dense(v, grb.GRB_FP32, out=out, present=False)
+        assert got is out and none is None
+        host = out.cpu().numpy() if hasattr(out, "cpu") else out
+        assert np.array_equal(host, want)
+    with pytest.raises(ValueError):
+        grb.grb_vector_extract_dense(v, grb.GRB_FP32, out=torch.empty(n - 1, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        grb.grb_vector_extract_dense(v, grb.GRB_FP32, out=torch.empty(n, dtype=torch.float64))
+    grb.grb_free(v)
+
+
 def test_api_errors_are_immediate(grb, ctx):
     v = grb.grb_vector_new(ctx, grb.GRB_FP64, 10)
     u = grb.grb_vector_new(ctx, grb.GRB_FP64, 11)
