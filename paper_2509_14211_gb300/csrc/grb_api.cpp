@@ -228,8 +228,12 @@ grb_info grb_context_new(grb_context* ctx, grb_mode mode, void* cuda_stream, grb
     const char* f = std::getenv("GRB_FUSION");
     if (f && f[0] == '0') c->fusion = false;
     c->status = buf_alloc(c, sizeof(int32_t));
-    if (!c->status.p || cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->stream) != cudaSuccess) {
+    c->sync = buf_alloc(c, sizeof(SyncWords));
+    if (!c->status.p || !c->sync.p || cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->sync.p, 0, sizeof(SyncWords), c->stream) != cudaSuccess) {
         cudaGetLastError();
+        buf_free(c, c->status);
+        buf_free(c, c->sync);
         delete c;
         return GRB_DEVICE_ERROR;
     }
@@ -900,6 +904,7 @@ grb_info grb_free(void** obj) {
         Ctx* c = reinterpret_cast<Ctx*>(*obj);
         cudaStreamSynchronize(c->stream);
         buf_free(c, c->status);
+        buf_free(c, c->sync);
         buf_free(c, c->red_scratch);
         buf_free(c, c->red_counter);
         pool_release_all(c);

@@ -106,7 +106,6 @@ struct TilePlan {
     DevBuf longfix;            // tiles whose split first row spans more than PR_LONG tiles
     int64_t nlong = 0;
     DevBuf part;               // 2 x grid_pr x 2 doubles (residual, dangling mass)
-    DevBuf sync;               // device counters (SyncWords)
     std::vector<DevBuf> loop_bufs;
     cudaGraphExec_t graph_exec = nullptr;
 };
@@ -194,6 +193,8 @@ struct Ctx {
     bool recording = false;
     std::vector<Stmt> body;
     DevBuf status;        // int32 device status word (bounded waits)
+    DevBuf sync;          // grid-barrier words (SyncWords) of every launch on the stream; cleared with the
+                          // status word after a device error
     cudaStream_t capture_stream = nullptr;   // CUDA-graph capture of device loops
     std::string err;
     std::vector<double> last_hist;    // residual history of the last device loop

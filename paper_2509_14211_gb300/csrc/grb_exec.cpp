@@ -134,7 +134,7 @@ static void sem_ops(grb_semiring s, int32_t& add, int32_t& mul) {
 
 static void plan_free(Ctx* c, TilePlan* p) {
     for (DevBuf* b : {&p->meta, &p->rowend_bits, &p->ne_rows, &p->empty_rows, &p->agg, &p->first, &p->fix,
-                      &p->longfix, &p->part, &p->sync})
+                      &p->longfix, &p->part})
         buf_free(c, *b);
     for (auto& b : p->loop_bufs) buf_free(c, b);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -157,9 +157,8 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
     p->fix = buf_alloc(c, sizeof(FixDesc) * p->ntiles);
     p->longfix = buf_alloc(c, sizeof(int32_t) * (p->ntiles + 3));
     p->part = buf_alloc(c, sizeof(double) * 2 * 2 * (size_t)c->sm_count * 8);
-    p->sync = buf_alloc(c, sizeof(SyncWords));
     if (!p->meta.p || !p->rowend_bits.p || !p->ne_rows.p || !p->empty_rows.p || !p->agg.p || !p->first.p ||
-        !p->fix.p || !p->longfix.p || !p->part.p || !p->sync.p) {
+        !p->fix.p || !p->longfix.p || !p->part.p) {
         plan_free(c, p);
         return GRB_OUT_OF_MEMORY;
     }
@@ -183,7 +182,6 @@ grb_info ensure_plan(Ctx* c, Matrix* A) {
     int32_t counts[3] = {0, 0, 0};
     if (!st)
         st = cuda_check(c, cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, c->stream), "plan");
-    if (!st) st = cuda_check(c, cudaMemsetAsync(p->sync.p, 0, sizeof(SyncWords), c->stream), "plan sync");
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "plan");
     if (st) {
         cudaStreamSynchronize(c->stream);
@@ -356,7 +354,7 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
     p.longfix = (const int32_t*)pl->longfix.p;
     p.nlong = (int32_t)pl->nlong;
     p.part = (double*)pl->part.p;
-    p.sync = (SyncWords*)pl->sync.p;
+    p.sync = (SyncWords*)c->sync.p;
     p.status = (int32_t*)c->status.p;
     p.spin_limit = c->spin_limit;
     return p;
@@ -388,6 +386,8 @@ grb_info read_status(Ctx* c) {
     if (e) return e;
     if (st != 0) {
         cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->stream);
+        // a barrier that gave up leaves its counter mid-crossing
+        cudaMemsetAsync(c->sync.p, 0, sizeof(SyncWords), c->stream);
         c->err = st == (int32_t)GRB_DEVICE_TIMEOUT ? "a bounded device-side wait ran out" : "device status error";
         return (grb_info)st;
     }

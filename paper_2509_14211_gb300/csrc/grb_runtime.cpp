@@ -185,7 +185,6 @@ void matrix_unref(Matrix* A) {
         buf_free(c, p->fix);
         buf_free(c, p->longfix);
         buf_free(c, p->part);
-        buf_free(c, p->sync);
         for (auto& b : p->loop_bufs) buf_free(c, b);
         if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
         delete p;

@@ -328,6 +328,35 @@ def test_device_wait_timeout_is_reported_not_hung(grb, ctx):
     grb.grb_free(s)
 
 
+def test_barrier_timeout_in_a_loop_leaves_the_next_solve_correct(grb):
+    """A grid barrier of the persistent PageRank loop that runs out of its
+    (here tiny) spin budget returns GRB_DEVICE_TIMEOUT instead of waiting on;
+    the barrier words it left mid-crossing are cleared with the status word,
+    so the next solve on the same matrix and context is right."""
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
+
+    n = 1 << 14   # ~43 CTAs: their arrivals at a barrier spread over far more than one poll
+    src, dst = graphgen.rmat_edges(14, 16, seed=5)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    try:
+        AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+        P = PageRankProblem(ctx, AT, n, 0.85, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+        grb.grb_context_set(ctx, grb.GRB_OPT_SPIN_LIMIT, 1)
+        with pytest.raises(grb.GrbError) as e:
+            P.run(-1.0, 30, "device")
+        assert e.value.code == grb.GRB_DEVICE_TIMEOUT
+        grb.grb_context_set(ctx, grb.GRB_OPT_SPIN_LIMIT, 1 << 24)
+        P.free()
+        P = PageRankProblem(ctx, AT, n, 0.85, grb.GRB_FP32, grb.GRB_FP64, "uniform")
+        assert P.run(-1.0, 30, "device") == 30
+        ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=0.85, tol=-1.0, itermax=30, mode="uniform")
+        assert np.sum(np.abs(P.rank().astype(np.float64) - ref)) <= 1e-6
+        P.free()
+        grb.grb_free(AT)
+    finally:
+        grb.grb_free(ctx)
+
+
 def test_allocator_failure_is_reported_and_recoverable(grb):
     """Allocator-failure injection: with the allocator refusing every
     request, a method that needs new device memory fails with
