@@ -101,3 +101,49 @@ def test_serve_argument_errors(grb, setup):
     with pytest.raises(grb.GrbError) as e:
         grb.grb_ppr_serve(AT, [0.0], [[n]])
     assert e.value.code == grb.GRB_INVALID_INDEX
+
+
+def test_rmat24_full_size_properties(grb):
+    """The serving workload at full size: R-MAT scale 24 (16.8 M vertices,
+    268 M raw edges), where the FP64 oracle is out of reach.  Properties that
+    hold at any size:
+    - personalised PageRank is linear in its teleport vector (uniform
+      dangling, r_0 = v): 15 bodies from seeds {a, b} equal the mean of those
+      from {a} and from {b}, L1 <= 1e-5 (FP32 rounding over 16.8 M entries);
+    - every result is non-negative with unit sum (|sum - 1| <= 1e-4);
+    - served queries stop at an L1 change <= tol before itermax, and each
+      equals the same query run alone, bit for bit."""
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    n = 1 << 24
+    src, dst = graphgen.rmat_edges(24, 16, seed=4)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    del src, dst
+    try:
+        rng = np.random.default_rng(24)
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        P = grb.grb_ppr_new(AT, D, 3)
+        try:
+            for s, S in enumerate(([a], [b], [a, b])):
+                grb.grb_ppr_set(P, s, np.array(S, np.int32), -1.0, 15)
+            grb.grb_ppr_run(P, 15)
+            r = [grb.grb_ppr_get(P, s, n).astype(np.float64) for s in range(3)]
+        finally:
+            grb.grb_free(P)
+        for x in r:
+            assert x.min() >= 0.0 and abs(x.sum() - 1.0) <= 1e-4
+        assert np.sum(np.abs(r[2] - 0.5 * (r[0] + r[1]))) <= 1e-5
+        del r
+        sets = graphgen.ppr_seed_sets(n, 4, 1, 64, seed=4, log_uniform=True)
+        out = grb.grb_ppr_serve(AT, np.zeros(4), sets, damping=D, tol=1e-6, itermax=200, chunk=4, n=n,
+                                want_ranks=True)
+        assert np.all(out["iters"] < 200) and np.all(out["resid"] <= 1e-6)
+        for q in (0, 3):
+            alone, its = _alone(grb, AT, n, sets[q], 1e-6, 200)
+            assert its == out["iters"][q]
+            assert np.array_equal(alone, out["ranks"][q])
+            assert alone.min() >= 0.0 and abs(alone.astype(np.float64).sum() - 1.0) <= 1e-4
+    finally:
+        grb.grb_free(AT)
+        grb.grb_free(ctx)
