@@ -111,10 +111,9 @@ __device__ __forceinline__ bool bit_of(const uint32_t* b, int i) { return (__ldg
 // every row; on a hit the k-tile's seed rows (sorted) are binary-searched.
 // The row is the same for the whole warp, so the control flow is uniform.
 template <int V>
-__device__ __forceinline__ void seed_terms(const PprParams& p, int kt, int i, int lane, float (&sv)[V]) {
+__device__ __forceinline__ void seed_terms_hit(const PprParams& p, int kt, int i, int lane, float (&sv)[V]) {
 #pragma unroll
     for (int v = 0; v < V; ++v) sv[v] = 0.f;
-    if (!bit_of(p.seedbits, i)) return;
     int lo = __ldg(p.seed_ptr + kt), hi = __ldg(p.seed_ptr + kt + 1);
     const int end = hi;
     while (lo < hi) {
@@ -131,6 +130,16 @@ __device__ __forceinline__ void seed_terms(const PprParams& p, int kt, int i, in
                 if (s % V == v) sv[v] = val;
         }
     }
+}
+
+template <int V>
+__device__ __forceinline__ void seed_terms(const PprParams& p, int kt, int i, int lane, float (&sv)[V]) {
+    if (!bit_of(p.seedbits, i)) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) sv[v] = 0.f;
+        return;
+    }
+    seed_terms_hit<V>(p, kt, i, lane, sv);
 }
 
 // Epilogue of row i for this lane's slots: r' = (seed + d D / n) + sum, the
@@ -157,6 +166,69 @@ __device__ __forceinline__ void ppr_row(const PprParams& p, int kt, int i, const
         if (L.act[v]) {
             L.res[v].add(fabsf(rold.x[v] - rn.x[v]));
             if (sink) L.dang[v].add(rn.x[v]);
+        }
+    }
+    if (all) {
+        rn.st_cs(p.r_new + o);
+        wn.st(p.w_new + o);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (L.act[v]) {
+                p.r_new[o + v] = rn.x[v];
+                p.w_new[o + v] = wn.x[v];
+            }
+    }
+}
+
+// A row without nonzeros (r' = seed + teleport term): its memory inputs,
+// loaded ahead so that several rows' loads are in flight together, and the
+// epilogue itself -- the same arithmetic as ppr_row with a zero sum.
+template <int V>
+struct EmptyIn {
+    Vec<V> rold;
+    float dd;
+    bool sink, seed;
+};
+
+template <int V>
+__device__ __forceinline__ EmptyIn<V> empty_row_inputs(const PprParams& p, int kt, int i, int lane, const Lane<V>& L) {
+    EmptyIn<V> a;
+    a.seed = bit_of(p.seedbits, i);
+    a.dd = 1.f;
+    a.sink = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) a.rold.x[v] = 0.f;
+    if (L.any) {
+        const size_t o = ((size_t)kt * (size_t)p.nrows + (size_t)i) * (PPR_LANES * V) + (size_t)lane * V;
+        a.rold.ld_cs(p.r_old + o);
+        a.dd = __ldg(p.dd + i);
+        a.sink = bit_of(p.sinkbits, i);
+    }
+    return a;
+}
+
+template <int V>
+__device__ __forceinline__ void empty_row(const PprParams& p, int kt, int i, int lane, Lane<V>& L,
+                                          const EmptyIn<V>& a) {
+    float sv[V];
+    if (a.seed) seed_terms_hit<V>(p, kt, i, lane, sv);   // uniform across the warp
+    else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) sv[v] = 0.f;
+    }
+    if (!L.any) return;
+    const size_t o = ((size_t)kt * (size_t)p.nrows + (size_t)i) * (PPR_LANES * V) + (size_t)lane * V;
+    Vec<V> rn, wn;
+    bool all = true;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        rn.x[v] = (sv[v] + L.tb[v]) + 0.f;
+        wn.x[v] = rn.x[v] / a.dd;
+        all = all && L.act[v];
+        if (L.act[v]) {
+            L.res[v].add(fabsf(a.rold.x[v] - rn.x[v]));
+            if (a.sink) L.dang[v].add(rn.x[v]);
         }
     }
     if (all) {
@@ -313,8 +385,9 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
 }
 
 // Phase A: the warp tiles, k-tile by k-tile (so the warps of the GPU share
-// one k-tile of w in L2 at a time), then the empty rows.  Tile t goes to the
-// same warp in every k-tile, so every slot sees the same summation order.
+// one k-tile of w in L2 at a time); the rows without nonzeros go to phase B.
+// Tile t goes to the same warp in every k-tile, so every slot sees the same
+// summation order.
 // The V = 4 tile loop keeps 16 gathered floats, 4 sums and 8 compensated
 // accumulators per lane: it gets the registers of one CTA per SM.
 template <int V>
@@ -332,11 +405,6 @@ __global__ void __launch_bounds__(PPR_BLOCK, (V == 4 ? 1 : 2)) ppr_tiles_kernel(
         if (!__any_sync(FULL, L.any)) continue;
         const bool all_live = __all_sync(FULL, L.any);   // every lane has a live slot
         for (int t = w0; t < p.ntiles; t += nwarps) ppr_tile<V>(p, kt, t, lane, L, all_live);
-        // rows without nonzeros: the epilogue with an empty sum
-        float zero[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) zero[v] = 0.f;
-        for (int e = w0; e < p.n_empty; e += nwarps) ppr_row<V>(p, kt, __ldg(p.empty_rows + e), zero, lane, L);
         lane_end<V>(kt, lane, warp, L, sm);
     }
     flush_slot_partials(p, sm);
@@ -344,9 +412,9 @@ __global__ void __launch_bounds__(PPR_BLOCK, (V == 4 ? 1 : 2)) ppr_tiles_kernel(
 
 // Phase B: rows split across tiles, one warp per (k-tile, tile) with a
 // fixup: the carries of the earlier tiles in tile order, then this tile's
-// part.
+// part; then the rows without nonzeros.
 template <int V>
-__global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_fixups_kernel(const __grid_constant__ PprParams p) {
+__global__ void __launch_bounds__(PPR_BLOCK, (V == 4 ? 1 : 2)) ppr_fixups_kernel(const __grid_constant__ PprParams p) {
     __shared__ PprSmem sm;
     zero_smem(sm);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -374,6 +442,25 @@ __global__ void __launch_bounds__(PPR_BLOCK, 2) ppr_fixups_kernel(const __grid_c
 #pragma unroll
             for (int v = 0; v < V; ++v) sum[v] += a.x[v];
             ppr_row<V>(p, kt, f.row, sum, lane, L);
+        }
+        // rows without nonzeros: the epilogue with an empty sum, four rows
+        // per warp per step -- their index loads, then their input loads,
+        // issued together (the tile kernel's registers stay with its loop)
+        const int w0 = blockIdx.x * NW + warp;
+        for (int e0 = w0; e0 < p.n_empty; e0 += 4 * nwarps) {
+            int i[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * nwarps;
+                i[u] = e < p.n_empty ? __ldg(p.empty_rows + e) : -1;
+            }
+            EmptyIn<V> in[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i[u] >= 0) in[u] = empty_row_inputs<V>(p, kt, i[u], lane, L);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i[u] >= 0) empty_row<V>(p, kt, i[u], lane, L, in[u]);
         }
         lane_end<V>(kt, lane, warp, L, sm);
     }
