@@ -519,8 +519,9 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
 }
 
 // Phase A over the tiles of this warp (static assignment, next tile's
-// coordinates prefetched).
-template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false, int NW = NWARP>
+// coordinates prefetched), then the rows without nonzeros (EU per thread per
+// step, their loads batched).
+template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false, int NW = NWARP, int EU = 1>
 __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
                                         Smem<T, NW>& sm) {
     const int warp = threadIdx.x >> 5;
@@ -541,7 +542,7 @@ __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& i
         }
         warp_tile<T, G, GMODE, NC, EPI, HOT>(p, t, cur, io, resid, dang, sm.w[warp]);
     }
-    empty_rows<T, G, NC, EPI>(p, io, resid, dang);
+    empty_rows<T, G, NC, EPI, EU>(p, io, resid, dang);
 }
 
 // Phase A with the gathers one tile deep: tile t+nwarps's gathers are issued
@@ -938,7 +939,9 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_batch_kernel(const 
     io.w = reinterpret_cast<const float*>(p.wbuf[from]);
     io.w_next = reinterpret_cast<float*>(p.wbuf[from ^ 1]);
     Acc<float> racc, dacc;
-    phase_a<float, float, G_W, true, EPI_MG>(p, io, racc, dacc, sm);
+    // per-row residual and dangling terms (folded per graph later): the
+    // order of the rows does not matter, so the empty ones go four at a time
+    phase_a<float, float, G_W, true, EPI_MG, false, NWARP, 4>(p, io, racc, dacc, sm);
     if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
     fixups<float, float, true, EPI_MG>(p, io, racc, dacc);
 }
