@@ -693,6 +693,7 @@ def main():
                    "timing": "CUDA events on the launching stream; inputs larger than L2 (CSR 0.29 GB)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "e2e": {"value": _job_gteps(ws, m, ITERS, e2e_t), "unit": "GTEPS", "ms_per_step": e2e_t,
+                "step_ms_min_median_max": [min(e2e_ms), float(np.median(e2e_ms)), max(e2e_ms)],
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "includes": "pinned COO upload, GPU CSR build, setup, 50 fused iterations, rank read-back"},
         "roofline": roofline,
