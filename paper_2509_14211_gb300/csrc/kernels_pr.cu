@@ -394,16 +394,17 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
     const int pre_i = f.pre_i >= 0 ? f.pre_i : 0;
     const RowIn<T>& pre = tv.pre;
     const T* v = tv.v;
-    // ---- row numbering: rows ending before this lane's nonzeros
+    // ---- row numbering: rows ending before this lane's nonzeros and in the
+    // whole tile, from the four bit planes of the per-lane counts (0..8)
     const int cnt = __popc(myf);
-    int incl = cnt;
+    const uint32_t below = (1u << lane) - 1u;
+    int before = 0, nrows = 0;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int o = __shfl_up_sync(FULLMASK, incl, off);
-        if (lane >= off) incl += o;
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t plane = __ballot_sync(FULLMASK, (cnt >> b) & 1);
+        before += __popc(plane & below) << b;
+        nrows += __popc(plane) << b;
     }
-    const int before = incl - cnt;
-    const int nrows = __shfl_sync(FULLMASK, incl, 31);
 
     // ---- per-lane segmented sums (row sums in ascending column order)
     T acc = (T)0;
@@ -418,18 +419,20 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
         }
     }
 
-    // ---- warp segmented (reduce-by-key) scan of the lane carries
-    const int key = idx;
+    // ---- warp segmented (reduce-by-key) scan of the lane carries: lane
+    // l - off carries into lane l's open row when no lane in (l - off, l]
+    // ends a row (`heads`: the lanes that end one)
+    const uint32_t heads = __ballot_sync(FULLMASK, cnt > 0);
     T val = acc;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const int k2 = __shfl_up_sync(FULLMASK, key, off);
         const T v2 = __shfl_up_sync(FULLMASK, val, off);
-        if (lane >= off && k2 == key) val = v2 + val;
+        const uint32_t span = lane >= off ? ((2u << lane) - 1u) ^ ((2u << (lane - off)) - 1u) : 0u;
+        if (lane >= off && (heads & span) == 0u) val = v2 + val;
     }
-    const int exk = __shfl_up_sync(FULLMASK, key, 1);
+    // the carry of lanes below ends this lane's first row (row `before`)
     const T exv = __shfl_up_sync(FULLMASK, val, 1);
-    if (lane > 0 && cnt > 0 && exk == before) ws.rowsum[before] = exv + ws.rowsum[before];
+    if (lane > 0 && cnt > 0) ws.rowsum[before] = exv + ws.rowsum[before];
     if (lane == 31) reinterpret_cast<T*>(p.agg)[t] = val;
     __syncwarp();
 
