@@ -17,18 +17,20 @@
 // rows are numbered in the compressed list of non-empty rows, and the empty
 // rows (~40% of an R-MAT graph) get their epilogue in a separate streaming
 // loop.  Warps are independent: per-lane segmented sums go to the warp's
-// shared-memory slice, and a warp-wide segmented scan (shuffles) joins rows
-// split across lanes.  Rows split across tiles are finished in a second
+// shared-memory slice, and a warp-wide segmented scan joins rows split across
+// lanes (ballots number the rows and mark where segments start; only the
+// carried values are shuffled).  Rows split across tiles are finished in a second
 // phase after a grid barrier, from per-tile carries (phase A writes them,
 // phase B adds them up in a fixed order); there are no cross-warp waits
 // inside a phase, and every barrier wait is bounded.  All reductions have a
 // fixed order, so results are bit-reproducible.
 //
-// Two epilogue flavours: LEAN (the PageRank loop: scalar teleport base,
-// residual and next gather value always produced, no presence array) is
-// compiled separately from the general one the planner uses for other
-// fused groups and for the unfused mxv, so the loop's per-row code carries
-// no run-time configuration checks.
+// Three epilogue flavours, compiled separately so that the loop's per-row
+// code carries no run-time configuration checks: LEAN (the PageRank loop:
+// scalar teleport base, residual and next gather value always produced, no
+// presence array), MG (a batch of independent graphs: per-graph teleport
+// and loop state, per-row residual and dangling terms) and the general one
+// the planner uses for other fused groups and for the unfused mxv.
 #include <climits>
 
 #include "grb_device.cuh"
@@ -323,8 +325,8 @@ __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, i
 // open at the end goes to agg[t].
 // The loads that start a tile: its column indices, row-end bits and the
 // first row a lane finishes.  They depend only on the tile index (and the
-// tile's metadata), so a warp issues them one tile ahead and their memory
-// latency overlaps the current tile's gathers.
+// tile's metadata), so a warp issues them ahead of use (one tile ahead, two
+// in the pipelined phase A) and their memory latency overlaps the gathers.
 struct TilePre {
     uint32_t meta;
     int4 ca, cb;
@@ -779,7 +781,7 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 // barrier, phase B, barrier, and every CTA folds the same partials in the
 // same order, so all CTAs take the same loop decision.
 //
-// HOT (one CTA of BLK = 1024 threads per SM): at the start of each body the
+// HOT (one CTA of BLK = PR_HOT_BLOCK threads per SM): at the start of each body the
 // CTA copies w[0, hot_n) into shared memory and serves gathers of those
 // columns from there.  With vertices numbered by descending out-degree these
 // are the most-gathered entries (for R-MAT, the first 32K of 4M vertices
@@ -1081,7 +1083,7 @@ void* pick_kernel(int32_t rank_type, int32_t gather_type, int32_t gmode, int per
 
 // The persistent loop with the shared-memory copy of the hottest gathered
 // entries: FP32 ranks and gathers only (the FP64 kernel's row-sum slices for
-// 32 warps would exceed the static shared-memory limit).
+// PR_HOT_BLOCK / 32 warps would exceed the static shared-memory limit).
 void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn, int32_t nst) {
     if (rank_type != GRB_FP32 || gather_type != GRB_FP32) return nullptr;
     void* k = nullptr;
