@@ -409,7 +409,8 @@ cudaError_t launch_ppr_extract(cudaStream_t st, int32_t n, const float* r, int32
 // FP32 divisor max(deg/damping, 1/damping) and sink bits from column counts.
 cudaError_t launch_ppr_divisor(cudaStream_t st, int32_t n, const int32_t* deg, double damping, float* dd,
                                uint32_t* sinkbits);
-int ppr_blocks_per_sm(int32_t vw);
+// CTAs per SM of the batched-PPR grid, for every vector width
+constexpr int PPR_CTAS_PER_SM = 2;
 
 // One body of a batch of graphs: phase A, grid barrier, phase B over the
 // block-diagonal A^T; reads rbuf[from]/wbuf[from], writes the other pair

@@ -194,7 +194,11 @@ grb_info alloc_layout(Ppr* P, int32_t vw) {
     P->pending.clear();
     P->cur = 0;
     P->dirty = true;
-    P->grid = ppr_blocks_per_sm(vw) * c->sm_count;
+    // the same grid at every width (two CTAs per SM; at width 4, whose CTAs
+    // need a whole SM's registers, that is two waves): each warp then takes
+    // the same tiles and rows, so every slot's sums are folded in the same
+    // order whatever the width
+    P->grid = PPR_CTAS_PER_SM * c->sm_count;
     const int64_t n = P->n, S = P->slots, nt = P->A->plan->ntiles;
     const size_t rb = sizeof(float) * (size_t)S * (size_t)n;
     for (int q = 0; q < 2; ++q) {

@@ -18,15 +18,16 @@
 // 256-nonzero tile (the same tile plan as the single-vector kernels) one by
 // one, all lanes adding their slots' values; row ends come from the row-end
 // bitmap.  Rows split across tiles are finished by ppr_fixups_kernel from
-// per-tile carries, and ppr_finish_kernel folds the per-CTA partials of every
-// slot in a fixed order.  The three kernels of an iteration are separated by
+// per-tile carries (it also takes the rows without nonzeros), and
+// ppr_finish_kernel folds the per-CTA partials of every slot in a fixed
+// order.  The three kernels of an iteration are separated by
 // kernel boundaries (the caller captures iterations in a CUDA graph), so
 // there are no device-side waits.
 //
 // Every slot's arithmetic (row sums in tile order, carries in tile order,
-// fixed-order folds over a grid that does not depend on k) is independent of
-// the other slots and of its position: a query gives the same bits alone and
-// in any batch.
+// fixed-order folds over a grid that depends neither on k nor on the vector
+// width) is independent of the other slots, of its position and of the
+// width: a query gives the same bits alone, in any batch and at any width.
 #include "grb_device.cuh"
 
 namespace grb {
@@ -575,26 +576,9 @@ inline int grid_1d(int64_t n, int block = 256) {
     return (int)(g < 1 ? 1 : g);
 }
 
-template <class K>
-int occ(K k) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, PPR_BLOCK, 0) != cudaSuccess) return 1;
-    return nb > 0 ? nb : 1;
-}
-
 bool valid_vw(int32_t vw) { return vw == 1 || vw == 2 || vw == 4; }
 
 }  // namespace
-
-int ppr_blocks_per_sm(int32_t vw) {
-    int a = 1, b = 1;
-    switch (vw) {
-        case 1: a = occ(ppr_tiles_kernel<1>); b = occ(ppr_fixups_kernel<1>); break;
-        case 2: a = occ(ppr_tiles_kernel<2>); b = occ(ppr_fixups_kernel<2>); break;
-        case 4: a = occ(ppr_tiles_kernel<4>); b = occ(ppr_fixups_kernel<4>); break;
-    }
-    return a < b ? a : b;
-}
 
 cudaError_t launch_ppr_tiles(cudaStream_t st, const PprParams& p, int grid) {
     if (!valid_vw(p.vw) || p.kt < 1 || p.kt * PPR_LANES * p.vw > PPR_MAX_SLOTS) return cudaErrorInvalidValue;
