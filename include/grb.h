@@ -204,8 +204,9 @@ grb_info grb_matrix_export_csr(grb_matrix A, int32_t* row_ptr, int32_t* col_idx,
                                int out_is_device);
 /* deg(j) = number of stored entries in column j of A (for A^T: the out-degree
  * of vertex j in the graph; §IV's out_degree).  deg must be an INT32 vector
- * of length ncols; vertices of degree 0 get no entry (GraphBLAS reduce
- * semantics). */
+ * of length ncols in A's context (else GRB_INVALID_VALUE); vertices of
+ * degree 0 get no entry (GraphBLAS reduce semantics).  The counts are
+ * computed once per matrix and kept with it. */
 grb_info grb_matrix_col_degree(grb_vector deg, grb_matrix A);
 
 /* ------------------------------------------------------------- vector */

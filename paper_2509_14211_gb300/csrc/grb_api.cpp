@@ -414,6 +414,7 @@ grb_info grb_matrix_col_degree(grb_vector deg, grb_matrix Am) {
     if (d->type != GRB_INT32) return GRB_DOMAIN_MISMATCH;
     if (d->n != A->ncols) return GRB_DIMENSION_MISMATCH;
     Ctx* c = d->ctx;
+    if (A->ctx != c) return GRB_INVALID_VALUE;   // the counts are cached on the matrix, in its context
     if (c->recording) return GRB_INVALID_VALUE;
     Version* v = new_version(c, false, GRB_INT32, d->n);
     v->vals = buf_alloc(c, sizeof(int32_t) * d->n);

@@ -308,6 +308,20 @@ def test_api_errors_are_immediate(grb, ctx):
     assert e.value.code == grb.GRB_DOMAIN_MISMATCH
     for h in (v, u, i):
         grb.grb_free(h)
+    # the column counts are cached on the matrix: a vector of another
+    # context is refused
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    A = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, 8, 8, np.array([0, 1, 2], np.int32),
+                                 np.array([1, 2, 3], np.int32), None, BUILD_FLAGS)
+    ctx2 = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    d2 = grb.grb_vector_new(ctx2, grb.GRB_INT32, 8)
+    with pytest.raises(grb.GrbError) as e:
+        grb.grb_matrix_col_degree(d2, A)
+    assert e.value.code == grb.GRB_INVALID_VALUE
+    grb.grb_free(d2)
+    grb.grb_free(ctx2)
+    grb.grb_free(A)
     for opt, bad in ((grb.GRB_OPT_HOT_BYTES, -1), (grb.GRB_OPT_HOT_BYTES, grb.GRB_HOT_BYTES_MAX + 1),
                      (grb.GRB_OPT_PERSISTENT, 4), (grb.GRB_OPT_SPIN_LIMIT, 0), (99, 1)):
         with pytest.raises(grb.GrbError) as e:
