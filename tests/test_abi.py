@@ -54,3 +54,22 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(grb, "_lib", None)
     with pytest.raises(ImportError):
         grb.load()
+
+
+def test_block_diagonal_edges_offsets_each_graph(lib):
+    """The graph-batch input: per-graph edge lists stacked with each graph's
+    vertex ids offset by the vertices before it; vptr marks the blocks (an
+    edgeless member keeps its block)."""
+    import numpy as np
+
+    import paper_2509_14211_gb300 as grb
+
+    graphs = [(3, [0, 1, 2], [1, 2, 0]), (2, [], []), (4, [3, 0], [0, 3])]
+    n, src, dst, vptr = grb.block_diagonal_edges(graphs)
+    assert n == 9 and vptr.tolist() == [0, 3, 5, 9]
+    assert src.dtype == np.int32 and dst.dtype == np.int32
+    assert src.tolist() == [0, 1, 2, 8, 5] and dst.tolist() == [1, 2, 0, 5, 8]
+    for k in range(len(graphs)):
+        lo, hi = vptr[k], vptr[k + 1]
+        inside = (src >= lo) & (src < hi)
+        assert np.all((dst[inside] >= lo) & (dst[inside] < hi))   # no edge leaves its block
