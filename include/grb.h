@@ -165,7 +165,8 @@ typedef struct grb_stats {
     int64_t device_bytes;       /* bytes currently held by the library */
     int64_t cache_hits;         /* signature-table hits (§III-C) */
     int64_t last_loop_kernel_ns;/* device time of the last device loop's kernels
-                                   (CUDA events on the context stream) */
+                                   (CUDA events on the context stream; reading
+                                   it waits for that loop) */
 } grb_stats;
 
 /* ------------------------------------------------------------ context */
@@ -178,6 +179,11 @@ grb_info grb_context_new(grb_context* ctx, grb_mode mode, void* cuda_stream,
                          grb_alloc_fn alloc, grb_free_fn free_fn, void* alloc_ctx);
 grb_info grb_context_set(grb_context ctx, grb_option opt, int64_t value);
 grb_info grb_context_stats(grb_context ctx, grb_stats* out);
+/* Device times in milliseconds of the last min(cap, 64) device loops run by
+ * grb_iterate_end on this context (CUDA events around the loop kernels on
+ * the context stream), oldest first; *n gets the count.  Waits for those
+ * loops.  Errors: GRB_NULL_POINTER (n NULL, or ms NULL with cap > 0). */
+grb_info grb_context_loop_times(grb_context ctx, double* ms, int64_t cap, int64_t* n);
 /* Runs every pending method of the context and synchronises its stream. */
 grb_info grb_context_wait(grb_context ctx);
 
@@ -283,20 +289,33 @@ grb_info grb_wait(void* obj, grb_wait_mode mode);
  * between grb_iterate_begin and grb_iterate_end are recorded as one loop body
  * instead of being run.  grb_iterate_end then executes
  *     while (iters < itermax && value(cond) > tol) { body; iters++; }
- * -- the loop test of the §IV listing, tested before each body.  When the
- * body matches the fused PageRank iteration the whole loop runs on the GPU
- * (one persistent kernel, or one fused kernel per iteration in a CUDA graph);
- * otherwise the body is replayed through the normal planner each iteration.
- * Every handle ends with the value the plain loop would give it. */
+ * -- the loop test of the §IV listing (Fig. "The PageRank implementation in
+ * AppGrB"), tested before each body.  When the body matches the fused
+ * PageRank iteration the whole loop runs on the GPU (one persistent kernel,
+ * or one fused kernel per iteration in a CUDA graph); otherwise the body is
+ * replayed through the normal planner each iteration.  Every handle ends with
+ * the value the plain loop would give it.
+ * In NONBLOCKING mode a device loop whose body count is fixed in advance
+ * (tol < 0: the loop test never fails, so *iters = itermax) only enqueues
+ * its work and returns, as a nonblocking method does (§II): its results are
+ * pending device values, and an execution error of the loop (a bounded
+ * device-side wait that ran out) is returned by the next call that waits --
+ * grb_wait, an extract, grb_scalar_get -- and sticks to what that call read.
+ * A loop that stops on its tolerance waits once, for its body count. */
 grb_info grb_iterate_begin(grb_context ctx);
 grb_info grb_iterate_end(grb_context ctx, grb_scalar cond, double tol, int64_t itermax,
                          int64_t* iters);
 
-/* Residual history of the last loop grb_iterate_end ran on the device:
- * hist[k] = the loop condition's value after body k, for k < *n (at most
- * cap written).  *mixed_phase (optional) is 1 when a mixed-precision loop
- * switched to the FP32 gather, 0 when it did not, -1 for other loops. */
-grb_info grb_iterate_history(grb_context ctx, double* hist, int64_t cap, int64_t* n, int32_t* mixed_phase);
+/* History of the last loop grb_iterate_end ran on the device (waits for
+ * it): hist[k] = the loop condition's value after body k (the §IV residual
+ * rdiff), dang[k] = the dangling mass of the rank after body k -- the sum of
+ * the rank over vertices without out-edges that the next body spreads
+ * uniformly (NaN for loops without it) -- for k < *n; at most cap entries of
+ * each written; hist and dang are optional.  *mixed_phase (optional) is 1
+ * when a mixed-precision loop switched to the FP32 gather, 0 when it did
+ * not, -1 for other loops. */
+grb_info grb_iterate_history(grb_context ctx, double* hist, double* dang, int64_t cap, int64_t* n,
+                             int32_t* mixed_phase);
 
 /* ------------------------------- batched personalised PageRank (extension)
  *
@@ -440,10 +459,11 @@ grb_info grb_prbatch_result(grb_prbatch B, float* ranks, int64_t* iters, double*
 /* ------------------------------------------------ allocation-free call */
 
 /* The paper has no counterpart to this call; it serves callers that cannot
- * allocate device memory when they need a reduction -- code running while a
- * stream is captured into a CUDA graph, code inside a host framework that
- * owns the whole device memory budget, latency-critical paths that cannot
- * pay for cudaMalloc's device synchronisation.
+ * allocate device memory when they need a reduction -- code inside a host
+ * framework that owns the whole device memory budget, code under a hard
+ * memory cap where a new allocation could fail at a bad moment,
+ * latency-critical paths that cannot pay for cudaMalloc's device
+ * synchronisation.
  *
  * *out = fold of the monoid over the n elements of the dense device array x
  * (type INT32, FP32 or FP64), accumulated in FP64 in a fixed order (block b
@@ -453,7 +473,10 @@ grb_info grb_prbatch_result(grb_prbatch B, float* ranks, int64_t* iters, double*
  * (4096 partial sums and a counter, ~32 KB) is a fixed device array that
  * every GPU loading the library keeps until the process exits.
  *  - n may be at most GRB_NOALLOC_MAX_N; larger n returns GRB_INVALID_VALUE
- *    before any GPU work.
+ *    before any GPU work.  n = 0 gives the monoid's identity (0, 1, -inf or
+ *    +inf for PLUS, TIMES, MAX, MIN).
+ *  - Each call clears the scratch's counter before its kernel runs, so a
+ *    call never depends on what an earlier one left in the array.
  *  - The first call on a device looks up the scratch array's device address
  *    (with that device current); make that first call before any stream
  *    capture.

@@ -12,7 +12,9 @@ by strings ("plus", "times", "div", "max", "min", "first", "second",
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, dense solves, brute-force adjacency, hand-checked
-GraphBLAS semantics in ``tests/golden/``).
+GraphBLAS semantics in ``tests/golden/``).  ``pagerank_par`` (``oracle_par.c``,
+the same listing with OpenMP loops over the rows, for timing the oracle on
+all host cores) is checked against ``pagerank`` there.
 """
 from __future__ import annotations
 
@@ -26,8 +28,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_SRC_PAR = os.path.join(_HERE, "oracle_par.c")
+_LIB_PAR = os.path.join(_HERE, "liboracle_par.so")
 _lock = threading.Lock()
 _lib = None
+_lib_par = None
 
 _BINOPS = {"first": 1, "second": 2, "plus": 3, "minus": 4, "times": 5, "div": 6, "max": 7,
            "min": 8, "abs_diff": 9, "max_div_by": 10}
@@ -47,11 +52,18 @@ class _OBinop(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc -O2, single-threaded)."""
+    """Compile oracle.c into liboracle.so (gcc -O2, single-threaded) and
+    oracle_par.c into liboracle_par.so (OpenMP when gcc has it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    if force or not os.path.exists(_LIB_PAR) or os.path.getmtime(_LIB_PAR) < os.path.getmtime(_SRC_PAR):
+        tmp = _LIB_PAR + f".tmp{os.getpid()}"
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC_PAR, "-lm"]
+        if subprocess.call(base[:2] + ["-fopenmp"] + base[2:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
+        os.replace(tmp, _LIB_PAR)
     return _LIB
 
 
@@ -247,3 +259,42 @@ def pagerank_edges(n: int, src, dst, **kw):
     """Convenience: build A^T and out-degrees from COO, then pagerank."""
     ptr, col = build_at(n, src, dst)
     return pagerank(ptr, col, out_degree(ptr, col), **kw)
+
+
+def _load_par():
+    global _lib_par
+    with _lock:
+        if _lib_par is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PAR)
+            lib.oracle_par_threads.argtypes = []
+            lib.oracle_par_threads.restype = ctypes.c_int
+            lib.oracle_pagerank_par.argtypes = [ctypes.c_int64, _i64p, _i64p, _i64p, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int64, ctypes.c_int, _f64p, _i64p, _f64p]
+            lib.oracle_pagerank_par.restype = ctypes.c_int
+            _lib_par = lib
+    return _lib_par
+
+
+def par_threads() -> int:
+    """Threads the multi-core variant runs on (OMP_NUM_THREADS, else all cores)."""
+    return int(_load_par().oracle_par_threads())
+
+
+def pagerank_par(ptr, col, outdeg, damping: float = 0.85, tol: float = 1e-10, itermax: int = 100,
+                 mode: str = "uniform"):
+    """The same pagerank_gap listing with OpenMP loops over the rows (for
+    timing on all host cores).  Returns (r, iterations, rdiff_history)."""
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int64)
+    outdeg = np.ascontiguousarray(outdeg, dtype=np.int64)
+    n = len(ptr) - 1
+    r = np.empty(n, dtype=np.float64)
+    hist = np.zeros(max(int(itermax), 1), dtype=np.float64)
+    iters = ctypes.c_int64()
+    _check(_load_par().oracle_pagerank_par(n, ptr.ctypes.data_as(_i64p), col.ctypes.data_as(_i64p),
+                                           outdeg.ctypes.data_as(_i64p), float(damping), float(tol), int(itermax),
+                                           _MODES[mode], r.ctypes.data_as(_f64p), ctypes.byref(iters),
+                                           hist.ctypes.data_as(_f64p)), "pagerank_par")
+    k = iters.value
+    return r, k, hist[:k].copy()

@@ -127,7 +127,8 @@ def _declare(lib):
         "grb_wait": [V, I],
         "grb_iterate_begin": [V],
         "grb_iterate_end": [V, V, D, I64, P(I64)],
-        "grb_iterate_history": [V, P(D), I64, P(I64), P(ctypes.c_int32)],
+        "grb_iterate_history": [V, P(D), P(D), I64, P(I64), P(ctypes.c_int32)],
+        "grb_context_loop_times": [V, P(D), I64, P(I64)],
         "grb_free": [P(V)],
         "grb_error": [V],
         "grb_selftest_wait_timeout": [V, I64],
@@ -177,7 +178,8 @@ def symbols():
                         "grb_scalar_new", "grb_scalar_set", "grb_scalar_get", "grb_scalar_apply_bind2nd",
                         "grb_apply", "grb_apply_bind2nd", "grb_apply_bind2nd_scalar", "grb_assign_scalar",
                         "grb_mxv", "grb_ewise_add", "grb_ewise_mult", "grb_reduce", "grb_wait",
-                        "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_free", "grb_error",
+                        "grb_iterate_begin", "grb_iterate_end", "grb_iterate_history", "grb_context_loop_times",
+                        "grb_free", "grb_error",
                         "grb_selftest_wait_timeout", "grb_reduce_dense_noalloc", "grb_ppr_new", "grb_ppr_slots", "grb_ppr_tune",
                         "grb_ppr_layout",
                         "grb_ppr_set", "grb_ppr_clear", "grb_ppr_run", "grb_ppr_status", "grb_ppr_get",
@@ -269,10 +271,20 @@ def grb_context_wait(ctx: int) -> None:
 # ----------------------------------------------------------------- matrix
 def grb_matrix_build_csr(ctx: int, type_: int, nrows: int, ncols: int, src, dst, vals=None,
                          flags: int = GRB_BUILD_TRANSPOSE | GRB_BUILD_DROP_SELF | GRB_BUILD_DEDUP) -> int:
-    """CSR from COO.  src/dst: int32 numpy arrays (host) or int32 torch CUDA
-    tensors (device; GRB_BUILD_DEVICE_PTRS is then added)."""
+    """CSR from COO.  src/dst: int32 numpy arrays or contiguous int32 torch
+    CPU tensors (host; pinned tensors let the library's upload run as a
+    direct DMA copy), or int32 torch CUDA tensors (device;
+    GRB_BUILD_DEVICE_PTRS is then added)."""
     if _is_device(src):
         flags |= GRB_BUILD_DEVICE_PTRS
+    elif hasattr(src, "data_ptr"):
+        import torch
+
+        for a in (src, dst):
+            if a.dtype != torch.int32 or not a.is_contiguous():
+                raise GrbError(GRB_INVALID_VALUE, "grb_matrix_build_csr", "host tensors must be contiguous int32")
+        if vals is not None:
+            vals = np.ascontiguousarray(vals.numpy() if hasattr(vals, "numpy") else vals, dtype=NP_TYPES[type_])
     else:
         src = np.ascontiguousarray(src, dtype=np.int32)
         dst = np.ascontiguousarray(dst, dtype=np.int32)
@@ -436,15 +448,30 @@ def grb_iterate_end(ctx, cond, tol, itermax) -> int:
     return it.value
 
 
-def grb_iterate_history(ctx):
-    """(residual history of the last device loop, mixed-precision phase)."""
+def grb_iterate_history(ctx, with_dang: bool = False):
+    """(residual history of the last device loop, mixed-precision phase), or
+    with with_dang (residuals, dangling masses, phase)."""
     n = ctypes.c_int64()
     ph = ctypes.c_int32()
-    _check(load().grb_iterate_history(ctx, None, 0, ctypes.byref(n), ctypes.byref(ph)), "grb_iterate_history", ctx)
+    _check(load().grb_iterate_history(ctx, None, None, 0, ctypes.byref(n), ctypes.byref(ph)),
+           "grb_iterate_history", ctx)
     h = np.empty(max(n.value, 1), dtype=np.float64)
-    _check(load().grb_iterate_history(ctx, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
-                                      ctypes.byref(n), ctypes.byref(ph)), "grb_iterate_history", ctx)
+    dg = np.empty(max(n.value, 1), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().grb_iterate_history(ctx, h.ctypes.data_as(dp), dg.ctypes.data_as(dp), n.value, ctypes.byref(n),
+                                      ctypes.byref(ph)), "grb_iterate_history", ctx)
+    if with_dang:
+        return h[:n.value], dg[:n.value], ph.value
     return h[:n.value], ph.value
+
+
+def grb_context_loop_times(ctx, cap: int = 64):
+    """Device times (ms) of the last device loops, oldest first (waits for them)."""
+    ms = np.zeros(max(int(cap), 1), np.float64)
+    n = ctypes.c_int64()
+    _check(load().grb_context_loop_times(ctx, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(cap),
+                                         ctypes.byref(n)), "grb_context_loop_times", ctx)
+    return ms[:n.value]
 
 
 # ------------------------------------------- batched personalised PageRank

@@ -275,8 +275,27 @@ grb_info grb_context_set(grb_context ctx, grb_option opt, int64_t value) {
 grb_info grb_context_stats(grb_context ctx, grb_stats* out) {
     Ctx* c = as_ctx(ctx);
     if (!c || !out) return GRB_NULL_POINTER;
+    c->stats.last_loop_kernel_ns = last_loop_kernel_ns(c);
     *out = c->stats;
     out->device_bytes = (int64_t)c->pool.held;
+    return GRB_SUCCESS;
+}
+
+grb_info grb_context_loop_times(grb_context ctx, double* ms, int64_t cap, int64_t* n) {
+    Ctx* c = as_ctx(ctx);
+    if (!c) return ctx ? GRB_UNINITIALIZED_OBJECT : GRB_NULL_POINTER;
+    if (!n || (cap > 0 && !ms) || cap < 0) return GRB_NULL_POINTER;
+    const int64_t have = std::min<int64_t>(c->loop_count, Ctx::LOOP_TIMES);
+    const int64_t k = std::min<int64_t>(have, cap);
+    for (int64_t q = 0; q < k; ++q) {
+        cudaEvent_t* ev = c->loop_ev[(c->loop_count - k + q) % Ctx::LOOP_TIMES];
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        if (e != cudaSuccess) return cuda_check(c, e, "loop times");
+        ms[q] = (double)t;
+    }
+    *n = k;
     return GRB_SUCCESS;
 }
 
@@ -911,6 +930,7 @@ grb_info grb_free(void** obj) {
         pool_release_all(c);
         cudaStreamSynchronize(c->stream);
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+        loop_resources_free(c);
         c->kind = Kind::DEAD;
         delete c;
     } else {
@@ -936,13 +956,19 @@ const char* grb_error(void* obj) {
     return "";
 }
 
-grb_info grb_iterate_history(grb_context ctx, double* hist, int64_t cap, int64_t* n, int32_t* mixed_phase) {
+grb_info grb_iterate_history(grb_context ctx, double* hist, double* dang, int64_t cap, int64_t* n,
+                             int32_t* mixed_phase) {
     Ctx* c = as_ctx(ctx);
     if (!c) return ctx ? GRB_UNINITIALIZED_OBJECT : GRB_NULL_POINTER;
     if (!n) return GRB_NULL_POINTER;
+    grb_info st = resolve_loop_history(c);
+    if (st) return st;
     *n = (int64_t)c->last_hist.size();
     if (hist)
         for (int64_t k = 0; k < *n && k < cap; ++k) hist[k] = c->last_hist[(size_t)k];
+    if (dang)
+        for (int64_t k = 0; k < *n && k < cap; ++k)
+            dang[k] = k < (int64_t)c->last_dang.size() ? c->last_dang[(size_t)k] : __builtin_nan("");
     if (mixed_phase) *mixed_phase = c->last_mixed_phase;
     return GRB_SUCCESS;
 }

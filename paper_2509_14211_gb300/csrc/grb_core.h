@@ -198,7 +198,23 @@ struct Ctx {
     cudaStream_t capture_stream = nullptr;   // CUDA-graph capture of device loops
     std::string err;
     std::vector<double> last_hist;    // residual history of the last device loop
+    std::vector<double> last_dang;    // its dangling-mass history (uniform dangling)
     int last_mixed_phase = -1;
+    // Pinned host staging of the last device loop's result slots and
+    // histories, filled by asynchronous copies behind the loop kernel:
+    // [0, 8) the loop slots, [8, 8 + cap) residuals, [8 + cap, 8 + 2 cap)
+    // dangling masses.  stage_ev marks the copies; the histories are read
+    // from the staging lazily (loop_pending) after that event.
+    double* stage = nullptr;
+    size_t stage_cap = 0;              // doubles
+    cudaEvent_t stage_ev = nullptr;
+    bool loop_pending = false;
+    int64_t loop_cap = 0;              // history capacity of the pending loop
+    bool loop_uniform = false, loop_mixed = false;
+    // CUDA events around the last LOOP_TIMES device loops' kernels (a ring)
+    static constexpr int LOOP_TIMES = 64;
+    cudaEvent_t loop_ev[LOOP_TIMES][2] = {};
+    int64_t loop_count = 0;
     std::vector<VectorH*> vhandles;   // live handles (grb_context_wait completes them)
     std::vector<ScalarH*> shandles;
 };
@@ -249,6 +265,9 @@ void ppr_destroy(Ppr* P);
 struct PrBatch;
 void prbatch_destroy(PrBatch* B);
 grb_info read_status(Ctx* c);
+grb_info resolve_loop_history(Ctx* c);
+int64_t last_loop_kernel_ns(Ctx* c);
+void loop_resources_free(Ctx* c);
 PrParams plan_params_of(Ctx* c, Matrix* A);
 int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n = 0,
             int32_t tma_stages = 0);

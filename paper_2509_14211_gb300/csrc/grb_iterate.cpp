@@ -192,6 +192,19 @@ void fulfil_scalar(Version* v, double value) {
     v->ready = true;
 }
 
+// The same with the value in a device slot (written in stream order).
+void fulfil_scalar_dev(Version* v, DevBuf& slot) {
+    if (v->producer) {
+        Node* nd = v->producer;
+        v->producer = nullptr;
+        node_destroy(nd);
+    }
+    v->host_known = false;
+    v->slot = slot;
+    slot = DevBuf();
+    v->ready = true;
+}
+
 template <class H>
 void save_handles(const std::vector<Stmt>& body, std::map<H*, Version*>& saved, H* Stmt::*field) {
     for (const Stmt& s : body) {
@@ -225,6 +238,87 @@ grb_info replay_dry(Ctx* c, const std::vector<Stmt>& body) {
 
 }  // namespace
 
+// Pinned host staging for a loop's result slots and histories (grown on
+// demand; copies of an earlier loop may still be landing in the old one).
+static grb_info ensure_stage(Ctx* c, size_t ndoubles) {
+    if (!c->stage_ev) {
+        grb_info st = cuda_check(c, cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming), "loop event");
+        if (st) return st;
+    }
+    if (c->stage_cap >= ndoubles) return GRB_SUCCESS;
+    grb_info st = cuda_check(c, cudaStreamSynchronize(c->stream), "loop staging");
+    if (st) return st;
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    const size_t cap = std::max<size_t>(ndoubles, 1024);
+    st = cuda_check(c, cudaMallocHost((void**)&c->stage, cap * sizeof(double)), "loop staging");
+    if (!st) c->stage_cap = cap;
+    return st;
+}
+
+// Events around the loop kernels: one pair of a ring per device loop.
+static cudaEvent_t* loop_events(Ctx* c) {
+    cudaEvent_t* ev = c->loop_ev[c->loop_count % Ctx::LOOP_TIMES];
+    for (int k = 0; k < 2; ++k)
+        if (!ev[k] && cudaEventCreate(&ev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            ev[k] = nullptr;
+        }
+    return ev[0] && ev[1] ? ev : nullptr;
+}
+
+grb_info resolve_loop_history(Ctx* c) {
+    if (!c->loop_pending) return GRB_SUCCESS;
+    grb_info st = cuda_check(c, cudaEventSynchronize(c->stage_ev), "loop history");
+    if (st) return st;
+    c->loop_pending = false;
+    int64_t K = 0;
+    std::memcpy(&K, &c->stage[0], sizeof(int64_t));
+    K = std::max<int64_t>(0, std::min<int64_t>(K, c->loop_cap));
+    const double* h = c->stage + 8;
+    c->last_hist.assign(h, h + K);
+    if (c->loop_uniform) c->last_dang.assign(h + c->loop_cap, h + c->loop_cap + K);
+    else c->last_dang.clear();
+    int32_t phase = 0;
+    std::memcpy(&phase, &c->stage[4], sizeof(int32_t));
+    c->last_mixed_phase = c->loop_mixed ? (int)phase : -1;
+    return GRB_SUCCESS;
+}
+
+int64_t last_loop_kernel_ns(Ctx* c) {
+    if (c->loop_count == 0) return c->stats.last_loop_kernel_ns;
+    cudaEvent_t* ev = c->loop_ev[(c->loop_count - 1) % Ctx::LOOP_TIMES];
+    float ms = 0.f;
+    if (ev[1] && cudaEventSynchronize(ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+        c->stats.last_loop_kernel_ns = (int64_t)(ms * 1e6);
+    cudaGetLastError();
+    return c->stats.last_loop_kernel_ns;
+}
+
+void loop_resources_free(Ctx* c) {
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    c->stage_ev = nullptr;
+    for (auto& pair : c->loop_ev)
+        for (cudaEvent_t& e : pair)
+            if (e) {
+                cudaEventDestroy(e);
+                e = nullptr;
+            }
+}
+
+// The device loop.  Everything -- loop kernel, copies of the result slots
+// and histories into pinned host memory, the permutes back to the caller's
+// vertex order -- is enqueued on the context's stream.  A loop whose body
+// count is fixed in advance (NONBLOCKING mode, tol < 0: every residual is
+// >= 0 > tol) returns without waiting: its outputs are device values ordered
+// behind the loop on the stream, and a device error (a bounded wait that ran
+// out, or a body count other than the one assumed) surfaces at the next call
+// that waits for the stream, as for any other pending method.  A loop that
+// stops on its tolerance waits once, for the body count.
 static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond, LoopMatch& lm, double tol,
                             int64_t itermax, double rd0, int64_t* iters_out) {
     NvtxRange range("grb: device PageRank loop");
@@ -247,11 +341,15 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     if (!st && rel) st = ensure_perm_copy(c, A, lm.d, false);
     if (!st && rel && lm.uniform) st = ensure_perm_copy(c, A, lm.sinks, true);
     if (st) return st;
+    const int iters = (int)std::min<int64_t>(itermax, INT_MAX - 16);
+    const int mode = (c->persistent == 2 && !mixed) ? 2 : 1;
+    const bool known = mode == 1 && c->mode == GRB_NONBLOCKING && tol < 0.0;
+    st = ensure_stage(c, 8 + 2 * (size_t)iters);
+    if (st) return st;
     Version* r0 = lm.r->cur;
     ver_ref(r0);
     const size_t tb = type_size(T) * (size_t)n, gb = type_size(G) * (size_t)n;
-    DevBuf r0full, rb[2], wb[2], w32[2], hist, slots;
-    const int iters = (int)std::min<int64_t>(itermax, INT_MAX);
+    DevBuf r0full, rb[2], wb[2], w32[2], hist, slots, cslot;
     rb[0] = buf_alloc(c, tb);
     rb[1] = buf_alloc(c, tb);
     wb[0] = buf_alloc(c, gb);
@@ -260,9 +358,11 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
         w32[0] = buf_alloc(c, sizeof(float) * n);
         w32[1] = buf_alloc(c, sizeof(float) * n);
     }
-    hist = buf_alloc(c, sizeof(double) * (size_t)iters);
+    hist = buf_alloc(c, sizeof(double) * 2 * (size_t)iters);
     slots = buf_alloc(c, sizeof(double) * 8);
-    if (!rb[0].p || !rb[1].p || !wb[0].p || !wb[1].p || !hist.p || !slots.p || (mixed && (!w32[0].p || !w32[1].p)))
+    if (known) cslot = buf_alloc(c, sizeof(double));
+    if (!rb[0].p || !rb[1].p || !wb[0].p || !wb[1].p || !hist.p || !slots.p || (mixed && (!w32[0].p || !w32[1].p)) ||
+        (known && !cslot.p))
         st = GRB_OUT_OF_MEMORY;
     const void* r0data = r0->vals.p;
     if (!st && r0->fmt == Fmt::ISO) {
@@ -319,6 +419,8 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     p.tol = tol;
     p.rdiff0 = rd0;
     p.hist = (double*)hist.p;
+    p.dhist = lm.uniform ? (double*)hist.p + iters : nullptr;
+    p.expect_iters = known ? iters : 0;
     p.iters_done = iters_done;
     p.r0 = r0data;
     p.rbuf[0] = rb[0].p;
@@ -331,10 +433,8 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
     p.wbuf32[1] = w32[1].p;
     p.mixed_phase = (int32_t*)(sl + 4);
 
-    const int mode = (c->persistent == 2 && !mixed) ? 2 : 1;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (!st && cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess)
-        cudaEventRecord(ev0, c->stream);
+    cudaEvent_t* ev = st ? nullptr : loop_events(c);
+    if (ev) cudaEventRecord(ev[0], c->stream);
     if (!st && mode == 1) {
         // shared-memory copy of the hottest entries of w: only useful when
         // the vertices are in degree order
@@ -382,33 +482,47 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
             st = cuda_check(c, e != cudaSuccess ? e : e2, "graph capture");
         }
         if (!st) st = cuda_check(c, cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
-        if (!st && ev0) cudaEventRecord(ev0, c->stream);   // time the graph's kernels only
+        if (!st && ev) cudaEventRecord(ev[0], c->stream);   // time the graph's kernels only
         if (!st) st = cuda_check(c, cudaGraphLaunch(exec, c->stream), "graph launch");
         c->stats.kernel_launches += 1 + iters;
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
     }
-    if (ev1) {
-        cudaEventRecord(ev1, c->stream);
-        if (!st && cudaEventSynchronize(ev1) == cudaSuccess) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) c->stats.last_loop_kernel_ns = (int64_t)(ms * 1e6);
+    if (ev) {
+        cudaEventRecord(ev[1], c->stream);
+        if (!st) c->loop_count++;
+    }
+    cudaGetLastError();
+    // result slots and histories -> pinned host staging, behind the loop
+    if (!st) {
+        st = cuda_check(c, cudaMemcpyAsync(c->stage, slots.p, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream),
+                        "loop result");
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(c->stage + 8, hist.p, sizeof(double) * 2 * (size_t)iters,
+                                               cudaMemcpyDeviceToHost, c->stream), "loop history");
+        if (!st) st = cuda_check(c, cudaEventRecord(c->stage_ev, c->stream), "loop history");
+        if (!st) {
+            c->loop_pending = true;
+            c->loop_cap = iters;
+            c->loop_uniform = lm.uniform;
+            c->loop_mixed = mixed;
+            c->stats.persistent_loops++;
         }
     }
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    cudaGetLastError();
-    double host_slots[8] = {0};
-    if (!st) st = cuda_check(c, cudaMemcpyAsync(host_slots, slots.p, sizeof(host_slots), cudaMemcpyDeviceToHost, c->stream), "loop result");
-    if (!st) st = read_status(c);
     int64_t K = 0;
-    if (!st) {
-        std::memcpy(&K, &host_slots[0], sizeof(int64_t));
-        c->stats.persistent_loops++;
-        c->last_hist.assign(iters > 0 ? (size_t)K : 0, 0.0);
-        if (K > 0)
-            st = cuda_check(c, cudaMemcpy(c->last_hist.data(), hist.p, sizeof(double) * K, cudaMemcpyDeviceToHost), "history");
-        c->last_mixed_phase = mixed ? (int)((int32_t*)(host_slots + 4))[0] : -1;
+    double rd_final = 0.0;
+    if (!st && known) {
+        K = iters;
+        st = cuda_check(c, cudaMemcpyAsync(cslot.p, sl + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->stream),
+                        "loop residual");
+    } else if (!st) {
+        // the body count is data-dependent: wait for it (and for the status)
+        st = read_status(c);
+        if (!st) st = resolve_loop_history(c);
+        if (!st) {
+            std::memcpy(&K, &c->stage[0], sizeof(int64_t));
+            rd_final = c->stage[1];
+        }
     }
     // back to the caller's vertex order: out[i] = buf[old2new[i]]
     auto unpermute = [&](DevBuf& b) -> grb_info {
@@ -441,13 +555,16 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
         st = replay_dry(c, body);
         if (!st) {
             fulfil_vector(lm.r->cur, rb[(K - 1) & 1]);
-            fulfil_scalar(cond->cur, host_slots[1]);
+            if (known) fulfil_scalar_dev(cond->cur, cslot);
+            else fulfil_scalar(cond->cur, rd_final);
         }
     }
     *iters_out = K;
-    cudaStreamSynchronize(c->stream);
     ver_unref(r0);
-    for (DevBuf* b : {&r0full, &rb[0], &rb[1], &wb[0], &wb[1], &w32[0], &w32[1], &hist, &slots}) buf_free(c, *b);
+    // back to the context's pool: later work on the same stream reuses them
+    // in stream order
+    for (DevBuf* b : {&r0full, &rb[0], &rb[1], &wb[0], &wb[1], &w32[0], &w32[1], &hist, &slots, &cslot})
+        buf_free(c, *b);
     return st;
 }
 
@@ -457,9 +574,15 @@ grb_info iterate_end(Ctx* c, ScalarH* cond, double tol, int64_t itermax, int64_t
     c->recording = false;
     *iters_out = 0;
     double rd = 0.0;
-    grb_info st = scalar_value(c, cond->cur, &rd);
-    if (st == GRB_NO_VALUE) rd = __builtin_inf();
-    else if (st) return st;
+    grb_info st = GRB_SUCCESS;
+    Version* cv = cond->cur;
+    if (cv->ready && !cv->err && cv->host_known) {
+        rd = cv->hval;   // set on the host: no need to wait for the stream
+    } else {
+        st = scalar_value(c, cv, &rd);
+        if (st == GRB_NO_VALUE) rd = __builtin_inf();
+        else if (st) return st;
+    }
     if (itermax == 0 || !(rd > tol)) return GRB_SUCCESS;
 
     LoopMatch lm;

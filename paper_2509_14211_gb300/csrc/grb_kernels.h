@@ -156,6 +156,9 @@ struct PrParams {
     int32_t iter_index = 0;      // per-iteration launch: index of this body
     double tol = -1.0;
     double* hist = nullptr;      // residual history (itermax doubles)
+    double* dhist = nullptr;     // dangling-mass history (itermax doubles; uniform dangling)
+    int32_t expect_iters = 0;    // persistent: > 0 when the host assumed this body count
+                                 // (fixed-count loop); any other count sets GRB_PANIC
     int64_t* iters_done = nullptr;
     const void* r0 = nullptr;    // persistent: input of body 0
     void* rbuf[2] = {nullptr, nullptr};

@@ -168,11 +168,15 @@ __device__ __forceinline__ void reduce_parts(const double* part, int n, double& 
     __syncthreads();
 }
 
-// Per-lane running sums of the residual and the dangling mass.  GB300's
-// FP64 pipe is narrow, so for FP32 ranks each lane keeps a compensated
-// (Kahan) FP32 sum -- error independent of the number of terms -- and hands
-// it to the FP64 cross-thread reduction once per body.  FP64 ranks sum in
-// FP64.
+// Per-lane running sums of the residual and the dangling mass (nonnegative
+// terms).  GB300's FP64 pipe is narrow, so for FP32 ranks each lane keeps its
+// sum as an unevaluated pair hi + lo of FP32 numbers ("double-float"): every
+// addition takes its exact rounding error from Knuth's TwoSum and folds it,
+// with the old low part, back in through Dekker's FastTwoSum (|s| >= |e|
+// holds for nonnegative terms).  That carries about 48 significant bits, so a
+// lane's sum of n terms is off by at most ~n * 2^-47 relative -- FP64-grade,
+// independent of the magnitude spread -- and hi + lo goes to the FP64
+// cross-thread reduction once per body.  FP64 ranks sum in FP64.
 template <class T>
 struct Acc {
     double s = 0.0;
@@ -182,14 +186,15 @@ struct Acc {
 
 template <>
 struct Acc<float> {
-    float s = 0.f, c = 0.f;
+    float hi = 0.f, lo = 0.f;
     __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
+        const float s = hi + x;
+        const float bv = s - hi;
+        const float e = ((hi - (s - bv)) + (x - bv)) + lo;
+        hi = s + e;
+        lo = e - (hi - s);
     }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 // Per-launch view of the gather / epilogue buffers.
@@ -769,6 +774,7 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
         if (p.tele_slot && p.want_dang) *p.tele_slot = schain_apply(p.chain, D);
         if (LEAN) {
             if (p.hist) p.hist[it] = R;
+            if (p.dhist) p.dhist[it] = D;
             *p.iters_done = it + 1;
         }
         p.sync->done = 0;
@@ -872,7 +878,10 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
         reduce_parts<T, BLK>(part, G_, R, D, sm);
         rd = round_to(p.resid_type, R);
         if (p.tele_from_slot) tele = (T)round_to(p.out.type, schain_apply(p.chain, D));
-        if (blockIdx.x == 0 && threadIdx.x == 0 && p.hist) p.hist[it] = rd;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (p.hist) p.hist[it] = rd;
+            if (p.dhist) p.dhist[it] = D;
+        }
         ++it;
         // mixed precision: once the residual is small -- or has stopped
         // falling, i.e. the BF16 rounding floor is reached (one body whose
@@ -927,6 +936,7 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
         if (p.dang_slot) *p.dang_slot = D;
         if (p.tele_slot) *p.tele_slot = (double)tele;
         *p.iters_done = it;
+        if (p.expect_iters > 0 && it != p.expect_iters) set_status(p.status, (int32_t)GRB_PANIC);
         if (p.mixed_phase) *p.mixed_phase = phase32;
         p.sync->launch += 1;
     }

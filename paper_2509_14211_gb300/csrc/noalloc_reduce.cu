@@ -1,15 +1,15 @@
 // Allocation-free variant of the library's deterministic reduction.
 //
 // Some callers cannot allocate device memory at the moment they need a
-// reduction: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a stream operation and breaks or is forbidden inside a
-// capture), code embedded in a host framework that owns the whole device
-// memory budget and forbids other allocations, and latency-critical paths
-// that cannot afford cudaMalloc's implicit device synchronisation.  For
-// them, grb_reduce_dense_noalloc takes caller-owned input and output buffers
-// and keeps its only scratch -- the per-block partial sums and the
-// last-block counter -- in a fixed file-scope __device__ array, so it never
-// calls cudaMalloc, cudaFree or an allocating library routine.
+// reduction: code embedded in a host framework that owns the whole device
+// memory budget and forbids allocations behind its back, code running under
+// a hard memory cap where a new allocation could fail at a bad moment, and
+// latency-critical paths that cannot afford cudaMalloc's implicit device
+// synchronisation.  For them, grb_reduce_dense_noalloc takes caller-owned
+// input and output buffers and keeps its only scratch -- the per-block
+// partial sums and the last-block counter -- in a fixed file-scope
+// __device__ array, so it never calls cudaMalloc, cudaFree or an allocating
+// library routine.
 #include <mutex>
 
 #include "grb_device.cuh"

@@ -342,11 +342,15 @@ def test_device_wait_timeout_is_reported_not_hung(grb, ctx):
     grb.grb_free(s)
 
 
-def test_barrier_timeout_in_a_loop_leaves_the_next_solve_correct(grb):
+@pytest.mark.parametrize("tol", [-1.0, 1e-30])
+def test_barrier_timeout_in_a_loop_leaves_the_next_solve_correct(grb, tol):
     """A grid barrier of the persistent PageRank loop that runs out of its
     (here tiny) spin budget returns GRB_DEVICE_TIMEOUT instead of waiting on;
     the barrier words it left mid-crossing are cleared with the status word,
-    so the next solve on the same matrix and context is right."""
+    so the next solve on the same matrix and context is right.  A loop with a
+    fixed body count (tol < 0) is only enqueued by grb_iterate_end, so its
+    error comes back from the first call that waits (here the rank read); a
+    loop that stops on its tolerance waits, and returns the error itself."""
     from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
 
     n = 1 << 14   # ~43 CTAs: their arrivals at a barrier spread over far more than one poll
@@ -357,8 +361,13 @@ def test_barrier_timeout_in_a_loop_leaves_the_next_solve_correct(grb):
         P = PageRankProblem(ctx, AT, n, 0.85, grb.GRB_FP32, grb.GRB_FP64, "uniform")
         grb.grb_context_set(ctx, grb.GRB_OPT_SPIN_LIMIT, 1)
         with pytest.raises(grb.GrbError) as e:
-            P.run(-1.0, 30, "device")
+            P.run(tol, 30, "device")
+            P.rank()
         assert e.value.code == grb.GRB_DEVICE_TIMEOUT
+        if tol < 0:   # the error sticks to what the failing wait read
+            with pytest.raises(grb.GrbError) as e:
+                P.rank()
+            assert e.value.code == grb.GRB_DEVICE_TIMEOUT
         grb.grb_context_set(ctx, grb.GRB_OPT_SPIN_LIMIT, 1 << 24)
         P.free()
         P = PageRankProblem(ctx, AT, n, 0.85, grb.GRB_FP32, grb.GRB_FP64, "uniform")

@@ -184,7 +184,12 @@ def test_deterministic_and_resumable(grb):
         grb.grb_iterate_begin(ctx)
         P.body()
         assert grb.grb_iterate_end(ctx, P.rdiff, -1.0, 8) == 8
-        np.testing.assert_allclose(P.rank(), a, rtol=0, atol=1e-9)
+        # bit for bit: the resumed loop's prologue sums the dangling mass of
+        # the checkpoint in another order than body 12's epilogue did, but both
+        # sums are FP64-accurate (~1e-14 relative) and the teleport is rounded
+        # to FP32 from them, so the two agree unless the sum sits within 1e-14
+        # of an FP32 rounding boundary
+        assert np.array_equal(P.rank(), a)
         P.free()
         grb.grb_free(AT)
     finally:
