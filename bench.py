@@ -271,7 +271,7 @@ def run_profile_case(args):
         grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, args.hot_bytes)
     if args.tma_stages is not None:
         grb.grb_context_set(ctx, grb.GRB_OPT_TMA_STAGES, args.tma_stages)
-    grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 1 if args.mixed else 0)
+    grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 2 if args.mixed else 0)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
     P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
@@ -298,18 +298,21 @@ def run_profile_case(args):
     grb.grb_free(ctx)
 
 
-MIXED_N_LOG2, MIXED_TOL = 24, 1e-6 * (1 - DAMPING) / DAMPING
+MIXED_TOL = 1e-6 * (1 - DAMPING) / DAMPING
 
 
-def run_mixed_leg(grb, torch, stream):
-    """Mixed precision on Erdos-Renyi 2^24 (out-degree 16, 2% sinks, seed 2):
-    BF16 gathers until the residual falls below 1e-3 (or stalls), then FP32,
-    to an L1 change of 1e-6 (1-d)/d; beside it the FP32-only loop to the same
-    stop.  Times are CUDA events around grb_iterate_end (graph resident)."""
+def run_mixed_leg(grb, torch, stream, log2n, modes):
+    """Mixed precision on Erdos-Renyi 2^log2n (out-degree 16, 2% sinks, seed
+    2): BF16 gathers until the residual falls below 1e-3 (or stalls), then
+    FP32, to an L1 change of 1e-6 (1-d)/d, beside the FP32-only loop to the
+    same stop.  `modes` are GRB_OPT_MIXED values: 1 lets the planner decide
+    (BF16 only when the FP32 gather vector exceeds L2), 2 forces BF16, 0 is
+    FP32 throughout.  Times are CUDA events around grb_iterate_end (graph
+    resident)."""
     import graphgen
     from paper_2509_14211_gb300.pagerank import BUILD_FLAGS, PageRankProblem
 
-    n = 1 << MIXED_N_LOG2
+    n = 1 << log2n
     src, dst = graphgen.er_edges(n, 16, p_dangling=0.02, seed=2)
     ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
     grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, 1)
@@ -317,10 +320,12 @@ def run_mixed_leg(grb, torch, stream):
     del src, dst
     m = grb.grb_matrix_nvals(AT)
     P = PageRankProblem(ctx, AT, n, DAMPING, grb.GRB_FP32, grb.GRB_FP64, "uniform")
-    out = {"workload": "Erdos-Renyi 2^24 vertices, out-degree 16, 2% sinks, seed 2, uniform dangling",
-           "n": n, "m": m, "stop_l1_change": MIXED_TOL}
+    out = {"workload": f"Erdos-Renyi 2^{log2n} vertices, out-degree 16, 2% sinks, seed 2, uniform dangling",
+           "n": n, "m": m, "stop_l1_change": MIXED_TOL, "fp32_gather_vector_bytes": 4 * n,
+           "l2_bytes": int(torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size)}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for mixed in (1, 0):
+    names = {0: "fp32_only", 1: "planner", 2: "bf16_forced"}
+    for mixed in modes:
         grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, mixed)
         P.run(MIXED_TOL, 500, "device")          # warm-up (builds plans, sink bits)
         times, iters = [], 0
@@ -333,11 +338,13 @@ def run_mixed_leg(grb, torch, stream):
         hist, phase = grb.grb_iterate_history(ctx)
         r = P.rank().astype(np.float64)
         ms = sorted(times)[1]
-        key = "mixed_bf16_fp32" if mixed else "fp32_only"
-        out[key] = {"ms": ms, "iterations": int(iters), "gteps": m * iters / (ms * 1e-3) / 1e9,
-                    "final_l1_change": float(hist[-1]), "switched_to_fp32": bool(phase == 1) if mixed else None,
-                    "rank_sum": float(np.sum(r)), "rank_min": float(np.min(r))}
-    out["mixed_speedup"] = out["fp32_only"]["ms"] / out["mixed_bf16_fp32"]["ms"]
+        out[names[mixed]] = {"ms": ms, "iterations": int(iters), "gteps": m * iters / (ms * 1e-3) / 1e9,
+                             "final_l1_change": float(hist[-1]), "bf16_phase_used": phase >= 0,
+                             "switched_to_fp32": bool(phase == 1) if phase >= 0 else None,
+                             "rank_sum": float(np.sum(r)), "rank_min": float(np.min(r))}
+    for name in ("planner", "bf16_forced"):
+        if name in out and "fp32_only" in out:
+            out[name + "_speedup"] = out["fp32_only"]["ms"] / out[name]["ms"]
     P.free()
     grb.grb_free(AT)
     grb.grb_free(ctx)
@@ -668,7 +675,10 @@ def main():
     # the extension legs are single-GPU measurements: with several ranks only
     # the replicated main metric runs, so the N GPUs are held no longer
     legs = ws == 1
-    mixed_leg = run_mixed_leg(grb, torch, stream) if legs and not args.no_mixed else None
+    mixed_leg = mixed_leg26 = None
+    if legs and not args.no_mixed:
+        mixed_leg = run_mixed_leg(grb, torch, stream, 24, (1, 2, 0))
+        mixed_leg26 = run_mixed_leg(grb, torch, stream, 26, (1, 0))
     ppr_leg = run_ppr_leg(grb, torch, stream) if legs and not args.no_ppr else None
     serve_leg = run_serve_leg(grb) if legs and not args.no_serve else None
     batch_leg = run_batch_leg(grb, torch, stream) if legs and not args.no_batch else None
@@ -705,6 +715,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
         # the extension legs first (long), the main step's evidence last
         "mixed_er24": mixed_leg,
+        "mixed_er26": mixed_leg26,
         "batched_ppr_rmat20_k64": ppr_leg,
         "serving_rmat24": serve_leg,
         "graph_batch_512": batch_leg,

@@ -121,9 +121,14 @@ typedef enum {
     GRB_OPT_SPIN_LIMIT = 3,    /* iteration limit of device-side waits (>0) */
     GRB_OPT_MIXED_SWITCH = 4,  /* residual below which the BF16 gather switches to
                                   FP32, in units of 1e-9 (default 1e6, i.e. 1e-3) */
-    GRB_OPT_MIXED = 5,         /* 1: FP32 PageRank loops gather the rank in BF16
-                                  (FP32 accumulation) until the residual falls
-                                  below the switch, then in FP32; 0 (default) off */
+    GRB_OPT_MIXED = 5,         /* FP32 PageRank device loops gather the rank in
+                                  BF16 (FP32 accumulation) until the residual
+                                  falls below the switch, then in FP32:
+                                  0 (default) never; 1 when the FP32 gather
+                                  vector (4 n bytes) exceeds the L2 cache, the
+                                  planner's choice (smaller vectors stay
+                                  L2-resident, where BF16 saves nothing);
+                                  2 always */
     GRB_OPT_RELABEL = 6,       /* 1 (default): device loops run on a copy of the
                                   matrix with vertices numbered by descending
                                   out-degree (built once per matrix, cached; the

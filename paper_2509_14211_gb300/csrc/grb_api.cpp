@@ -258,7 +258,10 @@ grb_info grb_context_set(grb_context ctx, grb_option opt, int64_t value) {
             if (value <= 0) return GRB_INVALID_VALUE;
             c->mixed_switch = (double)value * 1e-9;
             return GRB_SUCCESS;
-        case GRB_OPT_MIXED: c->mixed = value != 0; return GRB_SUCCESS;
+        case GRB_OPT_MIXED:
+            if (value < 0 || value > 2) return GRB_INVALID_VALUE;
+            c->mixed = (int)value;
+            return GRB_SUCCESS;
         case GRB_OPT_RELABEL: c->relabel = value != 0; return GRB_SUCCESS;
         case GRB_OPT_TMA_STAGES:
             if (value != 0 && value != 2 && value != 3) return GRB_INVALID_VALUE;

@@ -180,7 +180,7 @@ struct Ctx {
     int persistent = 0;
     int64_t spin_limit = int64_t(1) << 24;
     double mixed_switch = 1e-3;
-    bool mixed = false;
+    int mixed = 0;        // 0 off, 1 when the FP32 gather vector exceeds L2, 2 always
     bool relabel = true;  // device loops run on the degree-ordered copy of the matrix
     int64_t hot_bytes = 160 * 1024;  // shared-memory copy of the hottest gathered entries
     int32_t tma_stages = 0;          // bulk-copy staging depth of the hot loop (0: register prefetch)

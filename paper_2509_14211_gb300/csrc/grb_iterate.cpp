@@ -323,7 +323,11 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
                             int64_t itermax, double rd0, int64_t* iters_out) {
     NvtxRange range("grb: device PageRank loop");
     const grb_type T = lm.T;
-    const bool mixed = c->mixed && T == GRB_FP32;
+    // BF16 gathers pay only once the FP32 gather vector (4n bytes) no
+    // longer fits in L2: while it does, a gather costs one L2 sector
+    // whatever its width, and the BF16 phase only adds bodies
+    const bool mixed = T == GRB_FP32 &&
+                       (c->mixed == 2 || (c->mixed == 1 && (size_t)lm.A->nrows * sizeof(float) > c->l2_bytes));
     const grb_type G = mixed ? GRB_BF16 : T;
     Matrix* A = lm.A;
     const int64_t n = A->nrows;

@@ -103,6 +103,33 @@ struct FixDesc {
 
 enum GatherMode : int32_t { G_W = 0, G_TD = 1, G_ISO = 2 };
 
+// Per-graph fold of a batch body, run inside the body's cooperative launch
+// after a grid barrier: the rows' residual and dangling terms are summed per
+// chunk (at most MG_CHUNK consecutive rows of one graph, a warp each), then
+// per graph over its chunks (a warp each), all in fixed orders; then the
+// body is counted, the graph's loop test applied and its next teleport
+// (1-d)/n_g + d D_g / n_g set.
+constexpr int MG_CHUNK = 1024;
+struct MgFinish {
+    int32_t ngraphs = 0;
+    const int64_t* vptr = nullptr;     // ngraphs + 1 row offsets
+    const float* row_res = nullptr;
+    const float* row_dang = nullptr;
+    int32_t nchunks = 0;
+    const int32_t* chunk_lo = nullptr;    // nchunks + 1 row offsets
+    const int32_t* chunk_graph = nullptr; // graph of each chunk
+    const int32_t* g_chunk = nullptr;     // ngraphs + 1 chunk offsets
+    double* chunk_part = nullptr;         // per chunk: residual, dangling mass
+    int32_t* active = nullptr;
+    int32_t* iters = nullptr;
+    int32_t itermax = 0;
+    double tol = 0.0;
+    double* resid = nullptr;
+    float* tele = nullptr;
+    int32_t* final_buf = nullptr;
+    double damping = 0.85;
+};
+
 // Fused row-gather kernel over the rows of a CSR matrix (merge-path tiles):
 //   s_i   = sum over j in row i of g(j),  g = w[j] | t[j]/d[j] | g_iso
 //   out_i = base_i + s_i (row non-empty) | base_i (row empty)   when has_base
@@ -184,25 +211,7 @@ struct PrParams {
     const float* g_tele = nullptr;
     float* row_res = nullptr;
     float* row_dang = nullptr;
-};
-
-// Per-graph fold of a batch body: one CTA per graph sums the rows' residual
-// and dangling terms in a fixed order, counts the body, applies the graph's
-// loop test and sets its next teleport (1-d)/n_g + d D_g / n_g.
-struct MgFinish {
-    int32_t ngraphs = 0;
-    const int64_t* vptr = nullptr;     // ngraphs + 1 row offsets
-    const float* row_res = nullptr;
-    const float* row_dang = nullptr;
-    int32_t* active = nullptr;
-    int32_t* iters = nullptr;
-    int32_t itermax = 0;
-    double tol = 0.0;
-    double* resid = nullptr;
-    float* tele = nullptr;
-    int32_t* final_buf = nullptr;
-    int32_t out_buf = 0;
-    double damping = 0.85;
+    MgFinish mg;                 // the per-graph folds at the end of each body
 };
 
 // Start state of every graph of a batch: r = 1/n_g, w = r ./ d, the first
@@ -420,7 +429,6 @@ constexpr int PPR_CTAS_PER_SM = 2;
 // (cooperative launch of grid CTAs).
 cudaError_t launch_pr_batch(cudaStream_t st, const PrParams& p, int from, int grid);
 int pr_batch_blocks_per_sm();
-cudaError_t launch_mg_finish(cudaStream_t st, const MgFinish& f);
 cudaError_t launch_mg_init(cudaStream_t st, const MgInit& a);
 // graph_of[i] = g for vptr[g] <= i < vptr[g+1]; *bad (device) += rows with
 // a column outside their block.

@@ -3,8 +3,8 @@
 // (graph g owns rows and columns vptr[g] .. vptr[g+1]); every body is one
 // cooperative launch of the fused tile kernel over all graphs' nonzeros (so
 // a launch is as large as the sum of the graphs, however small each one is)
-// plus one fold kernel with a CTA per graph, and a whole solve is captured
-// as one CUDA graph.  Each graph follows the §IV loop with uniform dangling
+// that ends with the per-graph folds, and a whole solve is captured as one
+// CUDA graph.  Each graph follows the §IV loop with uniform dangling
 // on its own: teleport (1-d)/n_g, its own dangling mass, residual and loop
 // test; a graph whose test fails keeps its rank while the others go on.
 //
@@ -31,6 +31,8 @@ struct PrBatch {
     double damping = 0.85;
     std::vector<int64_t> vptr_h;
     DevBuf vptr, graph_of, dd, sinkbits, row_res, row_dang, r[2], w[2];
+    DevBuf chunk_lo, chunk_graph, g_chunk, chunk_part;   // the fold's chunks (MG_CHUNK rows of one graph)
+    int32_t nchunks = 0;
     DevBuf active, iters, resid, tele, final_buf;
     int grid = 0;          // tuned cooperative grid (0: not tuned yet)
     std::vector<double> tune_ms;   // per candidate CTAs/SM, ms per body
@@ -71,15 +73,16 @@ PrParams batch_params(PrBatch* B) {
     p.g_tele = (const float*)B->tele.p;
     p.row_res = (float*)B->row_res.p;
     p.row_dang = (float*)B->row_dang.p;
-    return p;
-}
-
-MgFinish batch_finish(PrBatch* B) {
-    MgFinish f;
+    MgFinish& f = p.mg;
     f.ngraphs = B->ng;
     f.vptr = (const int64_t*)B->vptr.p;
     f.row_res = (const float*)B->row_res.p;
     f.row_dang = (const float*)B->row_dang.p;
+    f.nchunks = B->nchunks;
+    f.chunk_lo = (const int32_t*)B->chunk_lo.p;
+    f.chunk_graph = (const int32_t*)B->chunk_graph.p;
+    f.g_chunk = (const int32_t*)B->g_chunk.p;
+    f.chunk_part = (double*)B->chunk_part.p;
     f.active = (int32_t*)B->active.p;
     f.iters = (int32_t*)B->iters.p;
     f.itermax = (int32_t)std::min<int64_t>(B->itermax, INT32_MAX);
@@ -88,7 +91,7 @@ MgFinish batch_finish(PrBatch* B) {
     f.tele = (float*)B->tele.p;
     f.final_buf = (int32_t*)B->final_buf.p;
     f.damping = B->damping;
-    return f;
+    return p;
 }
 
 grb_info init_state(PrBatch* B) {
@@ -114,14 +117,8 @@ grb_info init_state(PrBatch* B) {
 // `iters` bodies starting from buffer `from`, on stream st.
 grb_info record_bodies(PrBatch* B, cudaStream_t st, int64_t iters, int from, int grid) {
     PrParams p = batch_params(B);
-    MgFinish f = batch_finish(B);
     cudaError_t e = cudaSuccess;
-    for (int64_t k = 0; k < iters && e == cudaSuccess; ++k) {
-        const int src = (int)((from + k) & 1);
-        e = launch_pr_batch(st, p, src, grid);
-        f.out_buf = src ^ 1;
-        if (e == cudaSuccess) e = launch_mg_finish(st, f);
-    }
+    for (int64_t k = 0; k < iters && e == cudaSuccess; ++k) e = launch_pr_batch(st, p, (int)((from + k) & 1), grid);
     return cuda_check(B->c, e, "batch body");
 }
 
@@ -148,7 +145,7 @@ grb_info run_bodies(PrBatch* B, int64_t iters) {
         B->exec_grid = B->grid;
     }
     st = cuda_check(c, cudaGraphLaunch(B->exec, c->stream), "batch launch");
-    c->stats.kernel_launches += 2 * iters;
+    c->stats.kernel_launches += iters;
     B->cur = (int)((B->cur + iters) & 1);
     return st;
 }
@@ -203,7 +200,8 @@ void prbatch_destroy(PrBatch* B) {
     cudaStreamSynchronize(c->stream);
     drop_graph(B);
     for (DevBuf* b : {&B->vptr, &B->graph_of, &B->dd, &B->sinkbits, &B->row_res, &B->row_dang, &B->r[0], &B->r[1],
-                      &B->w[0], &B->w[1], &B->active, &B->iters, &B->resid, &B->tele, &B->final_buf})
+                      &B->w[0], &B->w[1], &B->active, &B->iters, &B->resid, &B->tele, &B->final_buf, &B->chunk_lo,
+                      &B->chunk_graph, &B->g_chunk, &B->chunk_part})
         buf_free(c, *b);
     if (B->A && B->A != B->A_in) matrix_unref(B->A);
     matrix_unref(B->A_in);
@@ -255,14 +253,38 @@ grb_info grb_prbatch_new(grb_prbatch* out, grb_matrix Am, int32_t ngraphs, const
     B->resid = buf_alloc(c, sizeof(double) * ngraphs);
     B->tele = buf_alloc(c, sizeof(float) * ngraphs);
     B->final_buf = buf_alloc(c, sizeof(int32_t) * ngraphs);
+    // the fold's chunks: each graph's rows cut into pieces of at most
+    // MG_CHUNK rows (host-side, from the offsets; fixed for the batch)
+    std::vector<int32_t> clo, cgr, gch(ngraphs + 1);
+    for (int32_t g = 0; g < ngraphs; ++g) {
+        gch[g] = (int32_t)clo.size();
+        for (int64_t i = vptr[g]; i < vptr[g + 1]; i += MG_CHUNK) {
+            clo.push_back((int32_t)i);
+            cgr.push_back(g);
+        }
+    }
+    gch[ngraphs] = (int32_t)clo.size();
+    B->nchunks = (int32_t)clo.size();
+    clo.push_back((int32_t)n);
+    B->chunk_lo = buf_alloc(c, sizeof(int32_t) * clo.size());
+    B->chunk_graph = buf_alloc(c, sizeof(int32_t) * cgr.size());
+    B->g_chunk = buf_alloc(c, sizeof(int32_t) * gch.size());
+    B->chunk_part = buf_alloc(c, sizeof(double) * 2 * cgr.size());
     DevBuf deg = buf_alloc(c, sizeof(int32_t) * n), pres = buf_alloc(c, (size_t)n),
            bad = buf_alloc(c, sizeof(unsigned long long));
     for (DevBuf* b : {&B->vptr, &B->graph_of, &B->dd, &B->sinkbits, &B->row_res, &B->row_dang, &B->r[0], &B->r[1],
-                      &B->w[0], &B->w[1], &B->active, &B->iters, &B->resid, &B->tele, &B->final_buf, &deg, &pres, &bad})
+                      &B->w[0], &B->w[1], &B->active, &B->iters, &B->resid, &B->tele, &B->final_buf, &B->chunk_lo,
+                      &B->chunk_graph, &B->g_chunk, &B->chunk_part, &deg, &pres, &bad})
         if (!b->p) st = GRB_OUT_OF_MEMORY;
     unsigned long long nbad = 0;
     if (!st) st = cuda_check(c, cudaMemcpyAsync(B->vptr.p, vptr, sizeof(int64_t) * (ngraphs + 1),
                                                 cudaMemcpyHostToDevice, c->stream), "batch offsets");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(B->chunk_lo.p, clo.data(), sizeof(int32_t) * clo.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "batch chunks");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(B->chunk_graph.p, cgr.data(), sizeof(int32_t) * cgr.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "batch chunks");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(B->g_chunk.p, gch.data(), sizeof(int32_t) * gch.size(),
+                                                cudaMemcpyHostToDevice, c->stream), "batch chunks");
     if (!st) {
         c->stats.kernel_launches += 4;
         st = cuda_check(c, launch_mg_graph_of(c->stream, ngraphs, (const int64_t*)B->vptr.p, (int32_t)n,

@@ -368,22 +368,16 @@ struct TileVals {
 template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false>
 __device__ __forceinline__ TileVals<T> tile_issue(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io) {
     static_assert(PR_NZLANE == 8, "two 16-byte column loads per lane");
-    const int lane = threadIdx.x & 31;
-    const int kl = t * PR_NZTILE + lane * PR_NZLANE;
-    const int nvalid = min(max(p.nnz - kl, 0), PR_NZLANE);
     TileVals<T> tv;
     tv.pre.rold = (T)0;
     tv.pre.dd = (T)1;
     tv.pre.sinkword = 0;
     if (f.pre_i >= 0) tv.pre = row_inputs<T, G, NC, EPI>(p, io, f.pre_i);
     const int cols[PR_NZLANE] = {f.ca.x, f.ca.y, f.ca.z, f.ca.w, f.cb.x, f.cb.y, f.cb.z, f.cb.w};
+    // padding entries of the last tile hold column 0: the load is in bounds,
+    // and tile_finish discards its value
 #pragma unroll
-    for (int q = 0; q < PR_NZLANE; ++q) {
-        // padding entries of the last tile hold column 0: the load is in
-        // bounds, and its value is discarded
-        const T g = gather<T, G, GMODE, NC, HOT>(p, io, cols[q]);
-        tv.v[q] = q < nvalid ? g : (T)0;
-    }
+    for (int q = 0; q < PR_NZLANE; ++q) tv.v[q] = gather<T, G, GMODE, NC, HOT>(p, io, cols[q]);
     return tv;
 }
 
@@ -400,18 +394,43 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
     const uint32_t myf = (f.bits >> (kl & 31)) & 0xffu;
     const int pre_i = f.pre_i >= 0 ? f.pre_i : 0;
     const RowIn<T>& pre = tv.pre;
-    const T* v = tv.v;
+    T v[PR_NZLANE];
+#pragma unroll
+    for (int q = 0; q < PR_NZLANE; ++q) v[q] = tv.v[q];
+    if (t == p.ntiles - 1) {   // the last tile: drop the padding's values
+        const int nvalid = min(max(p.nnz - kl, 0), PR_NZLANE);
+#pragma unroll
+        for (int q = 0; q < PR_NZLANE; ++q)
+            if (q >= nvalid) v[q] = (T)0;
+    }
+
+    // ---- a tile in which no row ends (inside a long row: ~40% of the tiles
+    // of an R-MAT graph) is all carry: the lane sums and the warp scan only,
+    // the same additions in the same order as below when no lane ends a row
+    if (__all_sync(FULLMASK, myf == 0u)) {
+        T val = (T)0;
+#pragma unroll
+        for (int q = 0; q < PR_NZLANE; ++q) val += v[q];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T v2 = __shfl_up_sync(FULLMASK, val, off);
+            if (lane >= off) val = v2 + val;
+        }
+        if (lane == 31) reinterpret_cast<T*>(p.agg)[t] = val;
+        return;
+    }
+
     // ---- row numbering: rows ending before this lane's nonzeros and in the
     // whole tile, from the four bit planes of the per-lane counts (0..8)
     const int cnt = __popc(myf);
     const uint32_t below = (1u << lane) - 1u;
-    int before = 0, nrows = 0;
+    int before = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const uint32_t plane = __ballot_sync(FULLMASK, (cnt >> b) & 1);
         before += __popc(plane & below) << b;
-        nrows += __popc(plane) << b;
     }
+    const int nrows = (int)__reduce_add_sync(FULLMASK, (unsigned)cnt);
 
     // ---- per-lane segmented sums (row sums in ascending column order)
     T acc = (T)0;
@@ -428,14 +447,16 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
 
     // ---- warp segmented (reduce-by-key) scan of the lane carries: lane
     // l - off carries into lane l's open row when no lane in (l - off, l]
-    // ends a row (`heads`: the lanes that end one)
-    const uint32_t heads = __ballot_sync(FULLMASK, cnt > 0);
+    // ends a row.  With h the highest lane <= l that ends one (-1 if none),
+    // that is off <= l - h (and off <= l for the lane to exist).
+    const uint32_t heads = __ballot_sync(FULLMASK, cnt > 0) & (0xffffffffu >> (31 - lane));
+    const int h = heads ? 31 - __clz(heads) : -1;
+    const int lim = min(lane - h, lane);
     T val = acc;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const T v2 = __shfl_up_sync(FULLMASK, val, off);
-        const uint32_t span = lane >= off ? ((2u << lane) - 1u) ^ ((2u << (lane - off)) - 1u) : 0u;
-        if (lane >= off && (heads & span) == 0u) val = v2 + val;
+        if (off <= lim) val = v2 + val;
     }
     // the carry of lanes below ends this lane's first row (row `before`)
     const T exv = __shfl_up_sync(FULLMASK, val, 1);
@@ -942,9 +963,18 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
     }
 }
 
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULLMASK, x, off);
+    return x;
+}
+
 // One body of a batch of independent graphs (block-diagonal A^T): the same
-// tiles, barrier and fixups as a PageRank body, with the per-graph epilogue.
-// The per-graph folds run in mg_finish_kernel (a kernel boundary away).
+// tiles, barrier and fixups as a PageRank body, with the per-graph epilogue
+// (per-row residual and dangling terms), then -- after a grid barrier -- the
+// per-graph folds: chunk sums by warps over all CTAs, another barrier, a
+// warp per graph over its chunks.  Every sum has a fixed order whatever the
+// grid, so the results do not depend on the launch shape.
 __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_batch_kernel(const __grid_constant__ PrParams p) {
     __shared__ Smem<float> sm;
     const int from = p.iter_index & 1;
@@ -954,39 +984,59 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_batch_kernel(const 
     io.w = reinterpret_cast<const float*>(p.wbuf[from]);
     io.w_next = reinterpret_cast<float*>(p.wbuf[from ^ 1]);
     Acc<float> racc, dacc;
-    // per-row residual and dangling terms (folded per graph later): the
+    // per-row residual and dangling terms (folded per graph below): the
     // order of the rows does not matter, so the empty ones go four at a time
     phase_a<float, float, G_W, true, EPI_MG, false, NWARP, 4>(p, io, racc, dacc, sm);
     if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
     fixups<float, float, true, EPI_MG>(p, io, racc, dacc);
-}
+    if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
 
-constexpr int MG_BLOCK = 256;
-
-__global__ void __launch_bounds__(MG_BLOCK) mg_finish_kernel(const __grid_constant__ MgFinish f) {
-    __shared__ double red[MG_BLOCK / 32], red2[MG_BLOCK / 32];
-    const int g = blockIdx.x;
-    if (!f.active[g]) return;   // the same in the whole CTA
-    const int64_t lo = f.vptr[g], hi = f.vptr[g + 1];
-    double R = 0.0, D = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += MG_BLOCK) {
-        R += (double)f.row_res[i];
-        D += (double)f.row_dang[i];
+    const MgFinish& f = p.mg;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * NWARP + (threadIdx.x >> 5);
+    const int nw = gridDim.x * NWARP;
+    // chunk sums: lane-strided double-float sums of the rows' FP32 terms,
+    // then a fixed FP64 warp tree (chunks of finished graphs are skipped)
+    for (int c = gw; c < f.nchunks; c += nw) {
+        if (!__ldcg(f.active + __ldg(f.chunk_graph + c))) continue;   // the same in the warp
+        const int lo = __ldg(f.chunk_lo + c), hi = __ldg(f.chunk_lo + c + 1);
+        Acc<float> R, D;
+        for (int i = lo + lane; i < hi; i += 32) {
+            R.add(__ldcg(f.row_res + i));
+            D.add(__ldcg(f.row_dang + i));
+        }
+        const double r = warp_sum_d(R.value()), d = warp_sum_d(D.value());
+        if (lane == 0) {
+            f.chunk_part[2 * c] = r;
+            f.chunk_part[2 * c + 1] = d;
+        }
     }
-    R = block_sum_d<MG_BLOCK>(R, red);
-    D = block_sum_d<MG_BLOCK>(D, red2);
-    if (threadIdx.x == 0) {
-        const int32_t k = f.iters[g] + 1;
-        const double ng = (double)(hi - lo);
-        f.iters[g] = k;
-        f.resid[g] = R;
-        f.tele[g] = (float)((1.0 - f.damping) / ng + f.damping * D / ng);
-        if (!(R > f.tol) || k >= f.itermax) {
-            f.active[g] = 0;
-            f.final_buf[g] = f.out_buf;
+    if (!grid_sync(p.sync, p.status, p.spin_limit, gridDim.x, &sm.ok)) return;
+    for (int g = gw; g < f.ngraphs; g += nw) {
+        if (!__ldcg(f.active + g)) continue;
+        const int c0 = __ldg(f.g_chunk + g), c1 = __ldg(f.g_chunk + g + 1);
+        double R = 0.0, D = 0.0;
+        for (int c = c0 + lane; c < c1; c += 32) {
+            R += __ldcg(f.chunk_part + 2 * c);
+            D += __ldcg(f.chunk_part + 2 * c + 1);
+        }
+        R = warp_sum_d(R);
+        D = warp_sum_d(D);
+        if (lane == 0) {
+            const int32_t k = f.iters[g] + 1;
+            const double ng = (double)(__ldg(f.vptr + g + 1) - __ldg(f.vptr + g));
+            f.iters[g] = k;
+            f.resid[g] = R;
+            f.tele[g] = (float)((1.0 - f.damping) / ng + f.damping * D / ng);
+            if (!(R > f.tol) || k >= f.itermax) {
+                f.active[g] = 0;
+                f.final_buf[g] = from ^ 1;
+            }
         }
     }
 }
+
+constexpr int MG_BLOCK = 256;
 
 __global__ void __launch_bounds__(MG_BLOCK) mg_init_kernel(const __grid_constant__ MgInit a) {
     __shared__ double red[MG_BLOCK / 32];
@@ -1119,12 +1169,6 @@ cudaError_t launch_pr_batch(cudaStream_t st, const PrParams& p0, int from, int g
     PrParams p = p0;
     p.iter_index = from;
     return coop_launch(pr_batch_kernel, grid, st, p);
-}
-
-cudaError_t launch_mg_finish(cudaStream_t st, const MgFinish& f) {
-    if (f.ngraphs <= 0) return cudaSuccess;
-    mg_finish_kernel<<<f.ngraphs, MG_BLOCK, 0, st>>>(f);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_mg_init(cudaStream_t st, const MgInit& a) {

@@ -103,10 +103,12 @@ def test_serve_argument_errors(grb, setup):
     assert e.value.code == grb.GRB_INVALID_INDEX
 
 
+@pytest.mark.slow
 def test_rmat24_full_size_properties(grb):
     """The serving workload at full size: R-MAT scale 24 (16.8 M vertices,
-    268 M raw edges), where the FP64 oracle is out of reach.  Properties that
-    hold at any size:
+    268 M raw edges).  Two served queries are checked against the FP64 oracle
+    at their body counts (L1 <= 1e-6; a few minutes of host CPU), and
+    properties that hold at any size:
     - personalised PageRank is linear in its teleport vector (uniform
       dangling, r_0 = v): 15 bodies from seeds {a, b} equal the mean of those
       from {a} and from {b}, L1 <= 1e-5 (FP32 rounding over 16.8 M entries);
@@ -119,6 +121,8 @@ def test_rmat24_full_size_properties(grb):
     src, dst = graphgen.rmat_edges(24, 16, seed=4)
     ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    ptr, col = oracle.build_at(n, src, dst)
+    od = oracle.out_degree(ptr, col)
     del src, dst
     try:
         rng = np.random.default_rng(24)
@@ -144,6 +148,11 @@ def test_rmat24_full_size_properties(grb):
             assert its == out["iters"][q]
             assert np.array_equal(alone, out["ranks"][q])
             assert alone.min() >= 0.0 and abs(alone.astype(np.float64).sum() - 1.0) <= 1e-4
+            S = np.unique(sets[q])
+            ref, k, _ = oracle.pagerank(ptr, col, od, damping=D, tol=-1.0, itermax=its, mode="uniform",
+                                        personal=SparseVec(n, S, np.full(len(S), 1.0 / len(S))))
+            assert k == its
+            assert np.sum(np.abs(out["ranks"][q].astype(np.float64) - ref)) <= 1e-6, q
     finally:
         grb.grb_free(AT)
         grb.grb_free(ctx)
