@@ -177,7 +177,9 @@ typedef struct grb_stats {
 /* ------------------------------------------------------------ context */
 
 /* New context bound to a CUDA device stream (NULL = legacy default stream) of
- * the current device.  alloc/free may be NULL (stream-ordered cudaMallocAsync
+ * the current device, in one of the §II execution modes (GrB_init's mode in
+ * the GraphBLAS C statement the paper builds on; §II "Nonblocking
+ * execution").  Every object made from it shares its mode and stream.  alloc/free may be NULL (stream-ordered cudaMallocAsync
  * is then used).  Errors: GRB_NULL_POINTER, GRB_INVALID_VALUE (bad mode),
  * GRB_DEVICE_ERROR (no usable GPU). */
 grb_info grb_context_new(grb_context* ctx, grb_mode mode, void* cuda_stream,
@@ -228,7 +230,12 @@ grb_info grb_vector_new(grb_vector* v, grb_context ctx, grb_type type, uint64_t 
  * rounded to v's type).  Stores no array (§III-A GrBVector(n, v)). */
 grb_info grb_vector_fill(grb_vector v, double value);
 /* Replace v's content by the given entries (idx ascending, distinct;
- * host or device pointers).  vals are doubles rounded to v's type. */
+ * host or device pointers; the GraphBLAS build of a sparse vector, the
+ * SparseVector of §III-A).  vals are doubles rounded to v's type.  The call
+ * waits for its copy.  Errors: GRB_NULL_POINTER, GRB_INVALID_VALUE (nvals >
+ * n), GRB_INVALID_INDEX (an index outside [0, n), or host indices not
+ * ascending; device indices are checked by the build kernel), GRB_OUT_OF_MEMORY;
+ * on an error v keeps its old value. */
 grb_info grb_vector_build(grb_vector v, const int32_t* idx, const double* vals, uint64_t nvals,
                           int ptrs_on_device);
 /* dst takes src's current value (O(1): the two share one immutable version;
@@ -238,7 +245,11 @@ grb_info grb_vector_size(uint64_t* n, grb_vector v);
 /* Number of entries; forces the vector's pending work. */
 grb_info grb_vector_nvals(uint64_t* nvals, grb_vector v);
 /* Copy the vector out as a dense array of its type (absent entries -> 0) and
- * an optional uint8 presence array.  Forces pending work. */
+ * an optional uint8 presence array (host pointers, or device pointers when
+ * out_is_device; n entries each, caller-owned).  Reading a result is a
+ * materialisation point (§II: a value leaves the library only through a
+ * method that waits; §III-B materialize), so pending work runs first and its
+ * execution errors are returned here. */
 grb_info grb_vector_extract_dense(grb_vector v, void* values, uint8_t* present, int out_is_device);
 
 /* ------------------------------------------------------------- scalar */
@@ -280,8 +291,10 @@ grb_info grb_ewise_add(grb_vector w, grb_vector mask, const grb_binop* accum, gr
 /* Intersection of index sets (§III-D element-wise multiplication). */
 grb_info grb_ewise_mult(grb_vector w, grb_vector mask, const grb_binop* accum, grb_binop op,
                         grb_vector u, grb_vector v, grb_desc desc);
-/* s accum= fold of the monoid over u's entries (identity when u is empty).
- * Accumulation runs in FP64 and rounds once to s's type. */
+/* s accum= fold of the monoid over u's entries (identity when u is empty):
+ * the reduce of the §IV listing (rdiff = reduce(+, t), Fig. "The PageRank
+ * implementation in AppGrB").  Accumulation runs in FP64 and rounds once to
+ * s's type; the fold order is fixed, so results are reproducible. */
 grb_info grb_reduce(grb_scalar s, const grb_binop* accum, grb_monoid m, grb_vector u, grb_desc desc);
 
 /* ------------------------------------------------------ materialisation */
@@ -400,9 +413,15 @@ grb_info grb_ppr_get(grb_ppr P, int32_t slot, float* ranks, int out_is_device);
  * in flight, retires the finished ones and repeats, sleeping while idle.
  * Slots: as many as mem_fraction of the free device memory holds (about
  * 16 n bytes each), at most `slots` when slots > 0 and GRB_PPR_MAX_SLOTS;
- * more arrivals than slots wait in arrival order.  The vector width is picked
- * by grb_ppr_tune before the first arrival.  A query's result is the one it
- * gets alone (grb_ppr).  Returns when every query is answered. */
+ * free memory is read again at every admission, and while other users of
+ * the device hold memory the slots in use stay below what mem_fraction of
+ * (free memory + the slots' own) allows; more arrivals than usable slots
+ * wait in arrival order.  The vector width is picked by grb_ppr_tune before
+ * the first arrival.  A slot query's result is the one it gets alone
+ * (grb_ppr); a query run on the single-vector loop (single_max) follows the
+ * same iteration and loop test with its rows summed in another order, so it
+ * agrees with the slot result to FP32 rounding.  Returns when every query
+ * is answered. */
 typedef struct grb_serve_config {
     double damping;
     double tol;            /* each query's loop test: rdiff > tol */
@@ -410,6 +429,9 @@ typedef struct grb_serve_config {
     int64_t chunk;         /* bodies per scheduling step (>= 1) */
     int32_t slots;         /* 0: limited by memory only */
     double mem_fraction;   /* (0, 1] */
+    int32_t single_max;    /* >= 0: while no query holds a slot and at most this
+                              many arrived queries wait, the oldest runs alone
+                              on the single-vector fused loop (0: never) */
 } grb_serve_config;
 
 typedef struct grb_serve_result {
@@ -422,6 +444,7 @@ typedef struct grb_serve_result {
     int64_t steps;         /* out: scheduling steps (graph launches) */
     int64_t max_in_flight; /* out */
     double wall_s;         /* out: time from start to the last answer */
+    int64_t single_queries;/* out: queries answered by the single-vector loop */
 } grb_serve_result;
 
 grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, const double* arrival_s,
@@ -495,10 +518,13 @@ grb_info grb_reduce_dense_noalloc(const void* x, grb_type type, uint64_t n, grb_
 
 /* -------------------------------------------------------------- misc */
 
-/* Release any handle (sets *obj to NULL).  Pending work that other objects
- * still need is kept. */
+/* Release any handle (sets *obj to NULL; GrB_free of the GraphBLAS
+ * statement, §II).  Pending work that other objects still need is kept
+ * (their method trees hold references, §III-A). */
 grb_info grb_free(void** obj);
-/* Last error message of a handle ("" if none). */
+/* Last error message of a handle ("" if none): the GraphBLAS error string
+ * of §II's error model (execution errors stick to the object that carries
+ * them).  The pointer stays valid until the handle is used again. */
 const char* grb_error(void* obj);
 /* Self-test of the bounded device-side wait: launches a grid-barrier kernel
  * in which one arrival never comes, with the given spin limit, and returns

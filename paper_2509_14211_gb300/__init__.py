@@ -68,14 +68,15 @@ class grb_stats(ctypes.Structure):
 
 class grb_serve_config(ctypes.Structure):
     _fields_ = [("damping", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int64),
-                ("chunk", ctypes.c_int64), ("slots", ctypes.c_int32), ("mem_fraction", ctypes.c_double)]
+                ("chunk", ctypes.c_int64), ("slots", ctypes.c_int32), ("mem_fraction", ctypes.c_double),
+                ("single_max", ctypes.c_int32)]
 
 
 class grb_serve_result(ctypes.Structure):
     _fields_ = [("latency_s", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("resid", ctypes.c_void_p),
                 ("ranks", ctypes.c_void_p), ("slots", ctypes.c_int32), ("vector_width", ctypes.c_int32),
                 ("steps", ctypes.c_int64),
-                ("max_in_flight", ctypes.c_int64), ("wall_s", ctypes.c_double)]
+                ("max_in_flight", ctypes.c_int64), ("wall_s", ctypes.c_double), ("single_queries", ctypes.c_int64)]
 
 
 def binop(code: int, k: float = 0.0) -> grb_binop:
@@ -538,10 +539,10 @@ def grb_ppr_get(P: int, slot: int, n: int, out=None):
 
 def grb_ppr_serve(AT: int, arrival_s, seed_sets, damping: float = 0.85, tol: float = 1e-6, itermax: int = 1000,
                   chunk: int = 4, slots: int = 0, mem_fraction: float = 0.5, n: int | None = None,
-                  want_ranks: bool = False):
+                  want_ranks: bool = False, single_max: int = 0):
     """Run the serving loop on host arrival times and seed sets.  Returns a
     dict: latency_s, iters, resid (numpy, per query), ranks (nq x n float32
-    when want_ranks), slots, steps, max_in_flight, wall_s."""
+    when want_ranks), slots, steps, max_in_flight, wall_s, single_queries."""
     arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
     nq = len(arrival)
     ptr = np.zeros(nq + 1, np.int64)
@@ -556,14 +557,15 @@ def grb_ppr_serve(AT: int, arrival_s, seed_sets, damping: float = 0.85, tol: flo
         if n is None:
             n = grb_matrix_nrows(AT)
         ranks = np.zeros((nq, n), np.float32)
-    cfg = grb_serve_config(float(damping), float(tol), int(itermax), int(chunk), int(slots), float(mem_fraction))
+    cfg = grb_serve_config(float(damping), float(tol), int(itermax), int(chunk), int(slots), float(mem_fraction),
+                           int(single_max))
     out = grb_serve_result(lat.ctypes.data, its.ctypes.data, res.ctypes.data,
-                           ranks.ctypes.data if ranks is not None else None, 0, 0, 0, 0, 0.0)
+                           ranks.ctypes.data if ranks is not None else None, 0, 0, 0, 0, 0.0, 0)
     _check(load().grb_ppr_serve(AT, ctypes.byref(cfg), nq, arrival.ctypes.data, ptr.ctypes.data, idx.ctypes.data,
                                 ctypes.byref(out)), "grb_ppr_serve", AT)
     return {"latency_s": lat, "iters": its, "resid": res, "ranks": ranks, "slots": out.slots,
             "vector_width": out.vector_width, "steps": out.steps,
-            "max_in_flight": out.max_in_flight, "wall_s": out.wall_s}
+            "max_in_flight": out.max_in_flight, "wall_s": out.wall_s, "single_queries": out.single_queries}
 
 
 # ------------------------------------------------ batch of independent graphs

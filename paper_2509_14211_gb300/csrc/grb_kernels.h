@@ -212,6 +212,10 @@ struct PrParams {
     float* row_res = nullptr;
     float* row_dang = nullptr;
     MgFinish mg;                 // the per-graph folds at the end of each body
+    // one personalised query (EPI_PERS loops): its seed rows (bitmap in the
+    // loop's vertex order) get the teleport term pers_val = (1-d)/|S|
+    const uint32_t* pers_bits = nullptr;
+    float pers_val = 0.f;
 };
 
 // Start state of every graph of a batch: r = 1/n_g, w = r ./ d, the first
@@ -451,6 +455,13 @@ constexpr size_t PR_SMEM_PER_BLOCK_MAX = 227 * 1024;
 constexpr int PR_HOT_BLOCK = 768;
 cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int32_t gather_type, int grid,
                       int persistent);
+// The persistent FP32 loop of one personalised query (p.pers_bits set; the
+// hot copy when p.hot_n > 0), its occupancy, and the scatter of its seeds
+// into the start vector and the seed bitmap.
+cudaError_t launch_pr_pers(cudaStream_t st, const PrParams& p, int grid);
+int pr_pers_blocks_per_sm(int32_t hot_n);
+cudaError_t launch_pr_seed_scatter(cudaStream_t st, int32_t nseeds, const int32_t* seeds, const int32_t* old2new,
+                                   float val, float* r0, uint32_t* bits);
 cudaError_t launch_barrier_selftest(cudaStream_t st, SyncWords* sync, int32_t* status, int64_t spin_limit, int grid);
 
 }  // namespace grb

@@ -216,30 +216,40 @@ struct TileIO {
     int hot_n;
 };
 
+// Epilogue kinds: the general one (any fused group), the PageRank loop body
+// (scalar teleport, residual and next gather value always produced), the
+// loop body of a batch of independent graphs (per-graph teleport and loop
+// state, per-row residual / dangling terms folded per graph later), and the
+// PageRank loop body of one personalised query (the loop body plus the
+// query's teleport term (1-d)/|S| on its seed rows).
+enum : int { EPI_GEN = 0, EPI_LEAN = 1, EPI_MG = 2, EPI_PERS = 3 };
+
 // Epilogue inputs of one row, loaded ahead of use.
-template <class T>
+template <class T, int EPI>
 struct RowIn {
     T rold;
     T dd;
     uint32_t sinkword;
 };
-
-// Epilogue kinds: the general one (any fused group), the PageRank loop body
-// (scalar teleport, residual and next gather value always produced), and
-// the loop body of a batch of independent graphs (per-graph teleport and
-// loop state, per-row residual / dangling terms folded per graph later).
-enum : int { EPI_GEN = 0, EPI_LEAN = 1, EPI_MG = 2 };
+template <class T>
+struct RowIn<T, EPI_PERS> {
+    T rold;
+    T dd;
+    uint32_t sinkword;
+    uint32_t seedword;
+};
 
 template <class T, class G, bool NC, int EPI>
-__device__ __forceinline__ RowIn<T> row_inputs(const PrParams& p, const TileIO<T, G>& io, int i) {
+__device__ __forceinline__ RowIn<T, EPI> row_inputs(const PrParams& p, const TileIO<T, G>& io, int i) {
     constexpr bool LEAN = EPI != EPI_GEN;
-    RowIn<T> in;
+    RowIn<T, EPI> in;
     in.rold = (T)0;
     in.dd = (T)1;
     in.sinkword = 0;
     if (LEAN || p.want_resid) in.rold = tload<T, NC>(io.r_old, i);
     if (LEAN || io.w_next || io.w32_next) in.dd = __ldg(reinterpret_cast<const T*>(p.dd) + i);
     if (p.want_dang) in.sinkword = __ldg(p.sinkbits + (i >> 5));
+    if constexpr (EPI == EPI_PERS) in.seedword = __ldg(p.pers_bits + (i >> 5));
     return in;
 }
 
@@ -247,7 +257,7 @@ __device__ __forceinline__ RowIn<T> row_inputs(const PrParams& p, const TileIO<T
 // next gather value, and its residual / dangling-mass contributions.
 template <class T, class G, int EPI>
 __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, G>& io, int i, T s, bool nonempty,
-                                             const RowIn<T>& in, Acc<T>& resid, Acc<T>& dang) {
+                                             const RowIn<T, EPI>& in, Acc<T>& resid, Acc<T>& dang) {
     T v;
     if constexpr (EPI == EPI_MG) {
         // row i of graph g: nothing once g's loop has ended (its rank stays
@@ -260,6 +270,16 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
         gstore<G>(io.w_next, i, (float)(v / in.dd));
         p.row_res[i] = (float)abs_c<T>(in.rold - v);
         p.row_dang[i] = ((in.sinkword >> (i & 31)) & 1u) ? (float)v : 0.f;
+        return;
+    }
+    if constexpr (EPI == EPI_PERS) {
+        // r_i = ((1-d)/|S| [i in S] + d D / n) + s_i
+        const T base = ((in.seedword >> (i & 31)) & 1u) ? (T)p.pers_val + io.tele : io.tele;
+        v = nonempty ? base + s : base;
+        io.out[i] = v;
+        resid.add(abs_c<T>(in.rold - v));
+        if ((in.sinkword >> (i & 31)) & 1u) dang.add(v);
+        gstore<G>(io.w_next, i, (float)(v / in.dd));
         return;
     }
     if (EPI == EPI_LEAN) {
@@ -357,18 +377,19 @@ __device__ __forceinline__ TilePre tile_pre(const PrParams& p, int t, uint32_t m
 
 // What a tile's loads deliver: the gathered values of the lane's nonzeros
 // and the epilogue inputs of the first row the lane finishes.
-template <class T>
+template <class T, int EPI>
 struct TileVals {
     T v[PR_NZLANE];
-    RowIn<T> pre;
+    RowIn<T, EPI> pre;
 };
 
 // First half of a tile: issue its gathers and the epilogue loads of the
 // lane's first row.  Nothing waits for them here.
 template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false>
-__device__ __forceinline__ TileVals<T> tile_issue(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io) {
+__device__ __forceinline__ TileVals<T, EPI> tile_issue(const PrParams& p, int t, const TilePre& f,
+                                                       const TileIO<T, G>& io) {
     static_assert(PR_NZLANE == 8, "two 16-byte column loads per lane");
-    TileVals<T> tv;
+    TileVals<T, EPI> tv;
     tv.pre.rold = (T)0;
     tv.pre.dd = (T)1;
     tv.pre.sinkword = 0;
@@ -383,7 +404,7 @@ __device__ __forceinline__ TileVals<T> tile_issue(const PrParams& p, int t, cons
 
 // Second half: row numbering, segmented sums, carries and the epilogue.
 template <class T, class G, bool NC, int EPI>
-__device__ __forceinline__ void tile_finish(const PrParams& p, int t, const TilePre& f, const TileVals<T>& tv,
+__device__ __forceinline__ void tile_finish(const PrParams& p, int t, const TilePre& f, const TileVals<T, EPI>& tv,
                                             const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
                                             WarpSmem<T>& ws) {
     const int lane = threadIdx.x & 31;
@@ -393,7 +414,7 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
     const int kl = t * PR_NZTILE + lane * PR_NZLANE;
     const uint32_t myf = (f.bits >> (kl & 31)) & 0xffu;
     const int pre_i = f.pre_i >= 0 ? f.pre_i : 0;
-    const RowIn<T>& pre = tv.pre;
+    const RowIn<T, EPI>& pre = tv.pre;
     T v[PR_NZLANE];
 #pragma unroll
     for (int q = 0; q < PR_NZLANE; ++q) v[q] = tv.v[q];
@@ -469,7 +490,7 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
     if (lane >= x_lo && lane < nrows) row_epilogue<T, G, EPI>(p, io, pre_i, ws.rowsum[lane], true, pre, resid, dang);
     for (int x = 32 + lane; x < nrows; x += 32) {
         const int i = ld_stream(p.ne_rows + rfirst + x);
-        const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, i);
+        const RowIn<T, EPI> in = row_inputs<T, G, NC, EPI>(p, io, i);
         row_epilogue<T, G, EPI>(p, io, i, ws.rowsum[x], true, in, resid, dang);
     }
     __syncwarp();
@@ -478,7 +499,7 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
 template <class T, class G, int GMODE, bool NC, int EPI, bool HOT = false>
 __device__ __forceinline__ void warp_tile(const PrParams& p, int t, const TilePre& f, const TileIO<T, G>& io,
                                           Acc<T>& resid, Acc<T>& dang, WarpSmem<T>& ws) {
-    const TileVals<T> tv = tile_issue<T, G, GMODE, NC, EPI, HOT>(p, t, f, io);
+    const TileVals<T, EPI> tv = tile_issue<T, G, GMODE, NC, EPI, HOT>(p, t, f, io);
     tile_finish<T, G, NC, EPI>(p, t, f, tv, io, resid, dang, ws);
 }
 
@@ -492,7 +513,7 @@ __device__ __forceinline__ void empty_rows(const PrParams& p, const TileIO<T, G>
     if constexpr (U == 1) {
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.n_empty; e += nthreads) {
             const int i = ld_stream(p.empty_rows + e);
-            const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, i);
+            const RowIn<T, EPI> in = row_inputs<T, G, NC, EPI>(p, io, i);
             row_epilogue<T, G, EPI>(p, io, i, (T)0, false, in, resid, dang);
         }
         return;
@@ -504,7 +525,7 @@ __device__ __forceinline__ void empty_rows(const PrParams& p, const TileIO<T, G>
             const int e = e0 + u * nthreads;
             i[u] = e < p.n_empty ? ld_stream(p.empty_rows + e) : -1;
         }
-        RowIn<T> in[U];
+        RowIn<T, EPI> in[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (i[u] >= 0) in[u] = row_inputs<T, G, NC, EPI>(p, io, i[u]);
@@ -524,7 +545,7 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p.ntiles; t += nthreads) {
         const FixDesc f = p.fix[t];
         if (f.row < 0 || t - f.ts > PR_LONG) continue;
-        const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, f.row);
+        const RowIn<T, EPI> in = row_inputs<T, G, NC, EPI>(p, io, f.row);
         T sum = (T)0;
         for (int tt = f.ts; tt < t; ++tt) sum += __ldcg(agg + tt);
         sum += __ldcg(first + t);
@@ -543,7 +564,7 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(FULLMASK, sum, off);
         if (lane == 0) {
             sum += (double)__ldcg(first + t);
-            const RowIn<T> in = row_inputs<T, G, NC, EPI>(p, io, f.row);
+            const RowIn<T, EPI> in = row_inputs<T, G, NC, EPI>(p, io, f.row);
             row_epilogue<T, G, EPI>(p, io, f.row, (T)sum, true, in, resid, dang);
         }
     }
@@ -592,10 +613,10 @@ __device__ __forceinline__ void phase_a_pipe(const PrParams& p, const TileIO<T, 
         f1.meta = 0u;
         if (t + nw < p.ntiles) f1 = tile_pre(p, t + nw, __ldg(p.tile_meta + t + nw));
         uint32_t meta2 = t + 2 * nw < p.ntiles ? __ldg(p.tile_meta + t + 2 * nw) : 0u;
-        TileVals<T> v0 = tile_issue<T, G, GMODE, false, EPI, HOT>(p, t, f0, io);
+        TileVals<T, EPI> v0 = tile_issue<T, G, GMODE, false, EPI, HOT>(p, t, f0, io);
         for (; t < p.ntiles; t += nw) {
             const int t1 = t + nw, t2 = t + 2 * nw, t3 = t + 3 * nw;
-            TileVals<T> v1;
+            TileVals<T, EPI> v1;
             if (t1 < p.ntiles) v1 = tile_issue<T, G, GMODE, false, EPI, HOT>(p, t1, f1, io);
             TilePre f2;
             f2.pre_i = -1;
@@ -816,9 +837,10 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 // L1/L2; the copy costs hot_n words per CTA per body from L2.
 static_assert(sizeof(Smem<float, PR_HOT_BLOCK / 32>) <= PR_HOT_STATIC_SMEM, "static shared memory bound");
 
-template <class T, class G, int BLK, bool HOT, int NST = 0>
+template <class T, class G, int BLK, bool HOT, int NST = 0, bool PERS = false>
 __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS))
     pr_persistent_kernel(const __grid_constant__ PrParams p) {
+    constexpr int EPI = PERS ? EPI_PERS : EPI_LEAN;
     __shared__ Smem<T, BLK / 32> sm;
     extern __shared__ int4 hot_raw[];
     // dynamic shared memory: [hot copy (hot_n words)][NST tile stages per
@@ -881,13 +903,13 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
         }
         Acc<T> racc, dacc;
         if constexpr (NST > 0)
-            phase_a_tma<T, G, G_W, EPI_LEAN, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
+            phase_a_tma<T, G, G_W, EPI, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
         else if constexpr (HOT)
-            phase_a_pipe<T, G, G_W, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
+            phase_a_pipe<T, G, G_W, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
         else
-            phase_a<T, G, G_W, false, EPI_LEAN, HOT, BLK / 32>(p, io, racc, dacc, sm);
+            phase_a<T, G, G_W, false, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
         if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
-        fixups<T, G, false, EPI_LEAN>(p, io, racc, dacc);
+        fixups<T, G, false, EPI>(p, io, racc, dacc);
         const double resid = block_sum_d<BLK>(racc.value(), sm.red);
         dang = block_sum_d<BLK>(dacc.value(), sm.red2);
         double* part = p.part + 2 * G_ * ((it + 1) & 1);
@@ -1085,6 +1107,19 @@ __global__ void barrier_selftest_kernel(SyncWords* sync, int32_t* status, int64_
     grid_sync(sync, status, spin_limit, gridDim.x + 1, &ok);
 }
 
+// Start vector and seed bitmap of one personalised query: r0[i] = val and
+// bit i set for every seed i (after renumbering by old2new when given).
+// r0 and bits are cleared beforehand; duplicate seeds write the same value.
+__global__ void pr_seed_scatter_kernel(int32_t nseeds, const int32_t* seeds, const int32_t* old2new, float val,
+                                       float* r0, uint32_t* bits) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseeds; k += gridDim.x * blockDim.x) {
+        int i = seeds[k];
+        if (old2new) i = old2new[i];
+        r0[i] = val;
+        atomicOr(bits + (i >> 5), 1u << (i & 31));
+    }
+}
+
 template <class K>
 cudaError_t coop_launch(K kernel, int grid, cudaStream_t st, const PrParams& p) {
     cudaLaunchConfig_t cfg = {};
@@ -1185,6 +1220,53 @@ cudaError_t launch_mg_graph_of(cudaStream_t st, int32_t ngraphs, const int64_t* 
     int grid = (n + 255) / 256;
     if (grid > 152 * 16) grid = 152 * 16;
     mg_graph_of_kernel<<<grid, 256, 0, st>>>(ngraphs, vptr, n, row_ptr, col_idx, graph_of, bad);
+    return cudaGetLastError();
+}
+
+// The persistent loop of one personalised query (FP32): with the hot copy
+// (degree-ordered matrix) or without.
+void* pick_pers(int32_t hot_n, size_t dyn) {
+    if (hot_n > 0) {
+        void* k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 0, true>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) return nullptr;
+        return k;
+    }
+    return (void*)pr_persistent_kernel<float, float, PR_BLOCK, false, 0, true>;
+}
+
+int pr_pers_blocks_per_sm(int32_t hot_n) {
+    const size_t dyn = hot_n > 0 ? pr_hot_dynamic_smem(hot_n, 0) : 0;
+    void* k = pick_pers(hot_n, dyn);
+    int nb = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, hot_n > 0 ? PR_HOT_BLOCK : PR_BLOCK, dyn) !=
+                  cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_pr_pers(cudaStream_t st, const PrParams& p, int grid) {
+    if (p.hot_n % 4 != 0 || p.hot_n > p.nrows || p.mixed || !p.pers_bits) return cudaErrorInvalidValue;
+    const size_t dyn = p.hot_n > 0 ? pr_hot_dynamic_smem(p.hot_n, 0) : 0;
+    void* k = pick_pers(p.hot_n, dyn);
+    if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(p.hot_n > 0 ? PR_HOT_BLOCK : PR_BLOCK);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&p};
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+cudaError_t launch_pr_seed_scatter(cudaStream_t st, int32_t nseeds, const int32_t* seeds, const int32_t* old2new,
+                                   float val, float* r0, uint32_t* bits) {
+    if (nseeds <= 0) return cudaSuccess;
+    pr_seed_scatter_kernel<<<(nseeds + 255) / 256, 256, 0, st>>>(nseeds, seeds, old2new, val, r0, bits);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,49 @@ def test_sparse_arrivals_and_memory_admission(grb, setup):
     assert np.all(out["iters"] > 0)
 
 
+def test_single_vector_loop_matches_slots_and_oracle(grb, setup):
+    """The single-vector loop (single_max): 12 queries arriving together with
+    single_max = 100 all run alone on the fused persistent loop; the same
+    queries through the slots (single_max = 0) take the same number of
+    bodies (or one more or fewer: the residual is summed in another order)
+    and agree within L1 1e-6, and both match the FP64 oracle at their body
+    counts."""
+    n, src, dst, AT = setup
+    sets = graphgen.ppr_seed_sets(n, 12, 1, 64, seed=14, log_uniform=True)
+    arr = np.zeros(12)
+    tol, itermax = 1e-7, 300
+    one = grb.grb_ppr_serve(AT, arr, sets, damping=D, tol=tol, itermax=itermax, chunk=4, slots=32,
+                            want_ranks=True, single_max=100)
+    slot = grb.grb_ppr_serve(AT, arr, sets, damping=D, tol=tol, itermax=itermax, chunk=4, slots=32,
+                             want_ranks=True, single_max=0)
+    assert one["single_queries"] == 12 and slot["single_queries"] == 0
+    assert np.all(one["resid"] <= tol) and np.all(one["iters"] < itermax)
+    assert np.all(np.abs(one["iters"] - slot["iters"]) <= 1)
+    ptr, col = oracle.build_at(n, src, dst)
+    od = oracle.out_degree(ptr, col)
+    for q in range(12):
+        S = np.unique(sets[q])
+        pv = SparseVec(n, S, np.full(len(S), 1.0 / len(S)))
+        ref, k, _ = oracle.pagerank(ptr, col, od, damping=D, tol=-1.0, itermax=int(one["iters"][q]),
+                                    mode="uniform", personal=pv)
+        assert np.sum(np.abs(one["ranks"][q].astype(np.float64) - ref)) <= 1e-6, q
+        assert one["ranks"][q].min() >= 0.0
+        if one["iters"][q] == slot["iters"][q]:
+            assert np.sum(np.abs(one["ranks"][q].astype(np.float64) - slot["ranks"][q])) <= 1e-6, q
+
+
+def test_low_load_runs_single_then_batches_a_burst(grb, setup):
+    """single_max = 2: queries spread out in time are answered alone on the
+    single-vector loop; a burst of 40 arrivals goes to the slots."""
+    n, _, _, AT = setup
+    sets = graphgen.ppr_seed_sets(n, 46, 1, 16, seed=15)
+    arr = np.concatenate([np.arange(6) * 0.03, 0.2 + np.zeros(40)])
+    out = grb.grb_ppr_serve(AT, arr, sets, damping=D, tol=1e-6, itermax=200, chunk=4, slots=64, single_max=2)
+    assert out["single_queries"] >= 6 and out["single_queries"] < 46
+    assert np.all(out["resid"] <= 1e-6) and np.all(out["iters"] > 0)
+    assert out["max_in_flight"] > 2
+
+
 def test_serve_argument_errors(grb, setup):
     n, _, _, AT = setup
     with pytest.raises(grb.GrbError) as e:
@@ -101,6 +144,12 @@ def test_serve_argument_errors(grb, setup):
     with pytest.raises(grb.GrbError) as e:
         grb.grb_ppr_serve(AT, [0.0], [[n]])
     assert e.value.code == grb.GRB_INVALID_INDEX
+    with pytest.raises(grb.GrbError) as e:
+        grb.grb_ppr_serve(AT, [0.0], [[n]], single_max=4)     # checked on the single-vector path too
+    assert e.value.code == grb.GRB_INVALID_INDEX
+    with pytest.raises(grb.GrbError) as e:
+        grb.grb_ppr_serve(AT, [0.0], [[1]], single_max=-1)
+    assert e.value.code == grb.GRB_INVALID_VALUE
 
 
 @pytest.mark.slow
@@ -153,6 +202,12 @@ def test_rmat24_full_size_properties(grb):
                                         personal=SparseVec(n, S, np.full(len(S), 1.0 / len(S))))
             assert k == its
             assert np.sum(np.abs(out["ranks"][q].astype(np.float64) - ref)) <= 1e-6, q
+            # the same query alone on the single-vector loop
+            one = grb.grb_ppr_serve(AT, np.zeros(1), [sets[q]], damping=D, tol=1e-6, itermax=200, chunk=4, n=n,
+                                    want_ranks=True, single_max=1)
+            assert one["single_queries"] == 1 and abs(int(one["iters"][0]) - its) <= 1
+            if int(one["iters"][0]) == its:
+                assert np.sum(np.abs(one["ranks"][0].astype(np.float64) - ref)) <= 1e-6, q
     finally:
         grb.grb_free(AT)
         grb.grb_free(ctx)
