@@ -271,6 +271,7 @@ def run_profile_case(args):
         grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, args.hot_bytes)
     if args.tma_stages is not None:
         grb.grb_context_set(ctx, grb.GRB_OPT_TMA_STAGES, args.tma_stages)
+    grb.grb_context_set(ctx, grb.GRB_OPT_ROW_BINS, 1 if args.row_bins else 0)
     grb.grb_context_set(ctx, grb.GRB_OPT_MIXED, 2 if args.mixed else 0)
     AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
     m = grb.grb_matrix_nvals(AT)
@@ -290,7 +291,7 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": True, "graph": args.graph, "mixed": args.mixed, "scale": args.scale, "n": n,
                       "m": m, "iters": done,
                       "loop_mode": args.loop_mode, "relabel": not args.no_relabel, "hot_bytes": args.hot_bytes,
-                      "tma_stages": args.tma_stages,
+                      "tma_stages": args.tma_stages, "row_bins": args.row_bins,
                       "ms_per_loop": ms, "kernel_ms": kms, "gteps": m * done / (ms * 1e-3) / 1e9,
                       "kernel_gteps": m * done / (kms * 1e-3) / 1e9}), flush=True)
     P.free()
@@ -520,6 +521,7 @@ def main():
     ap.add_argument("--no-relabel", action="store_true", help="profiling run on the matrix in its input vertex order")
     ap.add_argument("--hot-bytes", type=int, default=None, help="profiling run: shared-memory hot copy size")
     ap.add_argument("--tma-stages", type=int, default=None, help="profiling run: bulk-copy staging depth (0, 2, 3)")
+    ap.add_argument("--row-bins", action="store_true", help="profiling run: the row-length-binned body")
     ap.add_argument("--graph", default="rmat", choices=["rmat", "er"], help="profiling run: graph family")
     ap.add_argument("--case", default="pagerank", choices=["pagerank", "ppr", "batch"],
                     help="profiling run: the device PageRank loop, batched personalised PageRank, or the graph batch")

@@ -139,10 +139,15 @@ typedef enum {
                                   FP32 loop on a degree-ordered matrix uses for a
                                   copy of the most-gathered rank entries
                                   (0 .. GRB_HOT_BYTES_MAX; default 163840; 0 = off) */
-    GRB_OPT_TMA_STAGES = 8     /* that loop's tile arrays: 0 (default) = register
+    GRB_OPT_TMA_STAGES = 8,    /* that loop's tile arrays: 0 (default) = register
                                   prefetch one tile ahead; 2 or 3 = bulk copies
                                   (cp.async.bulk) into shared-memory stages that
                                   many tiles ahead (the hot copy shrinks to fit) */
+    GRB_OPT_ROW_BINS = 9       /* FP32 persistent PageRank loops: 0 (default) =
+                                  nonzero-split warp tiles; 1 = every row summed
+                                  by a group sized by its length (a thread, 4, 8
+                                  or 16 lanes, a warp, or a CTA for the hub rows),
+                                  no split rows and no fixup phase */
 } grb_option;
 
 #define GRB_HOT_BYTES_MAX 196608

@@ -45,6 +45,7 @@ GRB_WAIT_COMPLETE, GRB_WAIT_MATERIALIZE = 0, 1
 GRB_OPT_FUSION, GRB_OPT_PERSISTENT, GRB_OPT_SPIN_LIMIT, GRB_OPT_MIXED_SWITCH, GRB_OPT_MIXED, GRB_OPT_RELABEL = 1, 2, 3, 4, 5, 6
 GRB_OPT_HOT_BYTES = 7
 GRB_OPT_TMA_STAGES = 8
+GRB_OPT_ROW_BINS = 9
 GRB_HOT_BYTES_MAX = 196608
 
 NP_TYPES = {GRB_INT32: np.int32, GRB_FP32: np.float32, GRB_FP64: np.float64, GRB_BF16: np.uint16}

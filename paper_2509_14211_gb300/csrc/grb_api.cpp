@@ -267,6 +267,10 @@ grb_info grb_context_set(grb_context ctx, grb_option opt, int64_t value) {
             if (value != 0 && value != 2 && value != 3) return GRB_INVALID_VALUE;
             c->tma_stages = (int32_t)value;
             return GRB_SUCCESS;
+        case GRB_OPT_ROW_BINS:
+            if (value != 0 && value != 1) return GRB_INVALID_VALUE;
+            c->row_bins = value != 0;
+            return GRB_SUCCESS;
         case GRB_OPT_HOT_BYTES:
             if (value < 0 || value > GRB_HOT_BYTES_MAX) return GRB_INVALID_VALUE;
             c->hot_bytes = value;

@@ -108,6 +108,10 @@ struct TilePlan {
     DevBuf part;               // 2 x grid_pr x 2 doubles (residual, dangling mass)
     std::vector<DevBuf> loop_bufs;
     cudaGraphExec_t graph_exec = nullptr;
+    // row-length bins of the binned body (built on first use)
+    DevBuf bin_rows;
+    int32_t bin_off[7] = {0, 0, 0, 0, 0, 0, 0};
+    bool bins_built = false;
 };
 
 struct Matrix {
@@ -184,6 +188,7 @@ struct Ctx {
     bool relabel = true;  // device loops run on the degree-ordered copy of the matrix
     int64_t hot_bytes = 160 * 1024;  // shared-memory copy of the hottest gathered entries
     int32_t tma_stages = 0;          // bulk-copy staging depth of the hot loop (0: register prefetch)
+    bool row_bins = false;           // FP32 persistent loops: row-length-binned body instead of tiles
     bool dry = false;     // replaying a loop body to inspect its DAG: never execute
     DevBuf red_scratch;   // per-block partials of the reduction kernels
     DevBuf red_counter;   // last-block counter of the reduction kernels
@@ -256,6 +261,7 @@ VIn vin_of(const Version* v);
 size_t type_size(grb_type t);
 grb_info cuda_check(Ctx* c, cudaError_t e, const char* what);
 grb_info ensure_plan(Ctx* c, Matrix* A);
+grb_info ensure_bins(Ctx* c, Matrix* A);
 grb_info ensure_sinkbits(Ctx* c, Version* sinks);
 grb_info ensure_relabel(Ctx* c, Matrix* A);
 grb_info ensure_coldeg(Ctx* c, Matrix* A);
@@ -270,7 +276,7 @@ int64_t last_loop_kernel_ns(Ctx* c);
 void loop_resources_free(Ctx* c);
 PrParams plan_params_of(Ctx* c, Matrix* A);
 int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n = 0,
-            int32_t tma_stages = 0);
+            int32_t tma_stages = 0, bool bins = false);
 double round_host(grb_type t, double x);
 double host_binop(int32_t code, double k, double x, double y);
 bool guaranteed_full(const Version* v);

@@ -143,6 +143,45 @@ static void plan_free(Ctx* c, TilePlan* p) {
 
 // The matrix's row plan, built once; nothing is cached unless the whole plan
 // was built.
+// Row-length bins of the binned body: the non-empty rows by the group that
+// sums them (PR_BIN_MAX), ascending within each bin; once per matrix, from
+// the row offsets on the host.
+grb_info ensure_bins(Ctx* c, Matrix* A) {
+    grb_info st = ensure_plan(c, A);
+    if (st) return st;
+    TilePlan* pl = A->plan;
+    if (pl->bins_built) return GRB_SUCCESS;
+    const int64_t n = A->nrows;
+    std::vector<int32_t> rp((size_t)n + 1);
+    st = cuda_check(c, cudaMemcpyAsync(rp.data(), A->row_ptr.p, sizeof(int32_t) * (size_t)(n + 1),
+                                       cudaMemcpyDeviceToHost, c->stream), "row bins");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "row bins");
+    if (st) return st;
+    std::vector<int32_t> bins[6];
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t L = rp[(size_t)i + 1] - rp[(size_t)i];
+        if (L == 0) continue;
+        int b = 0;
+        while (b < 5 && L > PR_BIN_MAX[b]) ++b;
+        bins[b].push_back((int32_t)i);
+    }
+    std::vector<int32_t> all;
+    all.reserve((size_t)n);
+    for (int b = 0; b < 6; ++b) {
+        pl->bin_off[b] = (int32_t)all.size();
+        all.insert(all.end(), bins[b].begin(), bins[b].end());
+    }
+    pl->bin_off[6] = (int32_t)all.size();
+    pl->bin_rows = buf_alloc(c, sizeof(int32_t) * std::max<size_t>(all.size(), 1));
+    if (!pl->bin_rows.p) return GRB_OUT_OF_MEMORY;
+    if (!all.empty())
+        st = cuda_check(c, cudaMemcpyAsync(pl->bin_rows.p, all.data(), sizeof(int32_t) * all.size(),
+                                           cudaMemcpyHostToDevice, c->stream), "row bins");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "row bins");
+    if (!st) pl->bins_built = true;
+    return st;
+}
+
 grb_info ensure_plan(Ctx* c, Matrix* A) {
     if (A->plan) return GRB_SUCCESS;
     TilePlan* p = new TilePlan();
@@ -363,8 +402,8 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
 PrParams plan_params_of(Ctx* c, Matrix* A) { return plan_params(c, A); }
 
 int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persistent, int32_t hot_n,
-            int32_t tma_stages) {
-    int nb = pr_blocks_per_sm(T, G, gmode, persistent, hot_n, tma_stages);
+            int32_t tma_stages, bool bins) {
+    int nb = pr_blocks_per_sm(T, G, gmode, persistent, hot_n, tma_stages, bins);
     if (nb <= 0) {
         if (persistent == 1 && hot_n > 0) return 0;   // the hot-copy kernel cannot run: caller drops it
         nb = 1;

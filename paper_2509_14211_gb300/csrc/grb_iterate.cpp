@@ -439,26 +439,34 @@ static grb_info device_loop(Ctx* c, const std::vector<Stmt>& body, ScalarH* cond
 
     cudaEvent_t* ev = st ? nullptr : loop_events(c);
     if (ev) cudaEventRecord(ev[0], c->stream);
+    const bool bins = mode == 1 && c->row_bins && T == GRB_FP32 && !mixed;
+    if (!st && bins) {
+        st = ensure_bins(c, AL);
+        if (!st) {
+            p.bin_rows = (const int32_t*)AL->plan->bin_rows.p;
+            for (int b = 0; b < 7; ++b) p.bin_off[b] = AL->plan->bin_off[b];
+        }
+    }
     if (!st && mode == 1) {
         // shared-memory copy of the hottest entries of w: only useful when
         // the vertices are in degree order
         if (rel && !mixed && T == GRB_FP32 && c->hot_bytes >= 16) {
             // the staging buffers share the block's shared memory with the copy
-            p.tma_stages = c->tma_stages;
+            p.tma_stages = bins ? 0 : c->tma_stages;
             const int64_t stage_b = (int64_t)pr_hot_dynamic_smem(0, p.tma_stages);
             const int64_t room = (int64_t)PR_SMEM_PER_BLOCK_MAX - (int64_t)PR_HOT_STATIC_SMEM - stage_b;
             const int64_t bytes = std::min<int64_t>(c->hot_bytes, room);
             p.hot_n = (int32_t)(std::min<int64_t>(n, bytes / (int64_t)sizeof(float)) & ~(int64_t)3);
             if (p.hot_n <= 0) p.tma_stages = 0;
         }
-        int grid = p.hot_n > 0 ? pr_grid(c, AL, T, G, G_W, 1, p.hot_n, p.tma_stages) : 0;
+        int grid = p.hot_n > 0 ? pr_grid(c, AL, T, G, G_W, 1, p.hot_n, p.tma_stages, bins) : 0;
         if (grid <= 0) {
             p.hot_n = 0;
             p.tma_stages = 0;
-            grid = pr_grid(c, AL, T, G, G_W, 1);
+            grid = pr_grid(c, AL, T, G, G_W, 1, 0, 0, bins);
         }
         c->stats.kernel_launches++;
-        st = cuda_check(c, launch_pr(c->stream, p, T, G, grid, 1), "persistent pagerank loop");
+        if (!st) st = cuda_check(c, launch_pr(c->stream, p, T, G, grid, 1), "persistent pagerank loop");
     } else if (!st) {
         // prologue (no bodies) + one fused kernel per body, as a CUDA graph
         const int pgrid = pr_grid(c, AL, T, G, G_W, 1);

@@ -216,7 +216,15 @@ struct PrParams {
     // loop's vertex order) get the teleport term pers_val = (1-d)/|S|
     const uint32_t* pers_bits = nullptr;
     float pers_val = 0.f;
+    // row-length-binned body (persistent FP32 loop): the non-empty rows by
+    // group size, bins [bin_off[b], bin_off[b+1]) of bin_rows for b = thread,
+    // 4, 8, 16 lanes, warp, CTA (null: the nonzero-split tiles)
+    const int32_t* bin_rows = nullptr;
+    int32_t bin_off[7] = {0, 0, 0, 0, 0, 0, 0};
 };
+// Row-length bins of the binned body: rows of at most PR_BIN_MAX[b] nonzeros
+// go to bin b (groups of 1, 4, 8, 16, 32 lanes), longer ones to the CTA bin.
+constexpr int PR_BIN_MAX[5] = {4, 16, 64, 256, 8192};
 
 // Start state of every graph of a batch: r = 1/n_g, w = r ./ d, the first
 // teleport from the dangling mass of r, active = (itermax > 0 && 1 > tol).
@@ -444,7 +452,7 @@ cudaError_t launch_mg_graph_of(cudaStream_t st, int32_t ngraphs, const int64_t* 
 // (hot_n > 0: the persistent kernel with a hot copy of hot_n entries; 0 when
 // that configuration cannot run).
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n = 0,
-                     int32_t tma_stages = 0);
+                     int32_t tma_stages = 0, bool bins = false);
 // Dynamic shared memory of the hot persistent kernel.
 size_t pr_hot_dynamic_smem(int32_t hot_n, int32_t tma_stages);
 // Static shared memory of the hot persistent kernel (bytes, upper bound).

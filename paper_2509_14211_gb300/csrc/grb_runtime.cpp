@@ -186,6 +186,7 @@ void matrix_unref(Matrix* A) {
         buf_free(c, p->longfix);
         buf_free(c, p->part);
         for (auto& b : p->loop_bufs) buf_free(c, b);
+        buf_free(c, p->bin_rows);
         if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
         delete p;
     }

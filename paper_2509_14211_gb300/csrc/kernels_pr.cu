@@ -634,6 +634,103 @@ __device__ __forceinline__ void phase_a_pipe(const PrParams& p, const TileIO<T, 
     empty_rows<T, G, false, EPI, 4>(p, io, resid, dang);
 }
 
+// ------------------------------------------------ row-length-binned body
+// The alternative work decomposition (GRB_OPT_ROW_BINS): every non-empty row
+// is summed by one group of threads sized by the row's length -- a thread
+// (1-4 nonzeros), 4, 8 or 16 lanes (5-256), a warp (257-8192) or a whole
+// CTA (longer: the hub rows, whose per-warp sums meet in shared memory) --
+// so there are no split rows, no carries and no fixup phase, one grid
+// barrier per body instead of two.  The lanes of a group take the row's
+// nonzeros round-robin (the group's column loads are coalesced), gather from
+// the hot copy or L2, and fold their sums with a fixed butterfly.  Rows come
+// from per-bin lists (PR_BINS bins plus the empty rows); within a bin, the
+// groups of the grid take the rows round-robin.
+template <int GS, class T, class G, int EPI, bool HOT>
+__device__ __forceinline__ void bin_groups(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                           int lo_b, int hi_b) {
+    constexpr int NG = 32 / GS;   // groups per warp
+    const int lane = threadIdx.x & 31, sub = lane % GS, grp = lane / GS;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    // every warp makes the same number of rounds (the butterfly needs all lanes)
+    for (int base = lo_b + gw * NG; base < hi_b; base += nwarps * NG) {
+        const int k = base + grp;
+        const bool have = k < hi_b;
+        int i = 0, lo = 0, hi = 0;
+        if (have) {
+            i = ld_stream(p.bin_rows + k);
+            lo = __ldg(p.row_ptr + i);
+            hi = __ldg(p.row_ptr + i + 1);
+        }
+        RowIn<T, EPI> in{};
+        if (have && sub == 0) in = row_inputs<T, G, false, EPI>(p, io, i);
+        // four running sums per lane (shorter rounding chains, loads in flight)
+        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+        int e = lo + sub;
+        for (; e + 3 * GS < hi; e += 4 * GS) {
+            const int c0 = ld_stream(p.col_idx + e), c1 = ld_stream(p.col_idx + e + GS);
+            const int c2 = ld_stream(p.col_idx + e + 2 * GS), c3 = ld_stream(p.col_idx + e + 3 * GS);
+            a0 += gather<T, G, G_W, false, HOT>(p, io, c0);
+            a1 += gather<T, G, G_W, false, HOT>(p, io, c1);
+            a2 += gather<T, G, G_W, false, HOT>(p, io, c2);
+            a3 += gather<T, G, G_W, false, HOT>(p, io, c3);
+        }
+        for (; e < hi; e += GS) a0 += gather<T, G, G_W, false, HOT>(p, io, ld_stream(p.col_idx + e));
+        T acc = (a0 + a1) + (a2 + a3);
+        __syncwarp();
+#pragma unroll
+        for (int off = GS / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, off);
+        if (have && sub == 0) row_epilogue<T, G, EPI>(p, io, i, acc, true, in, resid, dang);
+    }
+}
+
+template <class T, class G, int EPI, bool HOT, int NW>
+__device__ __forceinline__ void bin_cta_rows(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                             int lo_b, int hi_b, T* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = lo_b + blockIdx.x; k < hi_b; k += gridDim.x) {   // the same in the whole CTA
+        const int i = __ldg(p.bin_rows + k);
+        const int lo = __ldg(p.row_ptr + i), hi = __ldg(p.row_ptr + i + 1);
+        RowIn<T, EPI> in{};
+        if (threadIdx.x == 0) in = row_inputs<T, G, false, EPI>(p, io, i);
+        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+        const int step = NW * 32;
+        int e = lo + (int)threadIdx.x;
+        for (; e + 3 * step < hi; e += 4 * step) {
+            const int c0 = ld_stream(p.col_idx + e), c1 = ld_stream(p.col_idx + e + step);
+            const int c2 = ld_stream(p.col_idx + e + 2 * step), c3 = ld_stream(p.col_idx + e + 3 * step);
+            a0 += gather<T, G, G_W, false, HOT>(p, io, c0);
+            a1 += gather<T, G, G_W, false, HOT>(p, io, c1);
+            a2 += gather<T, G, G_W, false, HOT>(p, io, c2);
+            a3 += gather<T, G, G_W, false, HOT>(p, io, c3);
+        }
+        for (; e < hi; e += step) a0 += gather<T, G, G_W, false, HOT>(p, io, ld_stream(p.col_idx + e));
+        T acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, off);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T sum = red[0];
+            for (int w = 1; w < NW; ++w) sum += red[w];
+            row_epilogue<T, G, EPI>(p, io, i, sum, true, in, resid, dang);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T, class G, int EPI, bool HOT, int NW>
+__device__ __forceinline__ void phase_bins(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
+                                           Smem<T, NW>& sm) {
+    bin_cta_rows<T, G, EPI, HOT, NW>(p, io, resid, dang, p.bin_off[5], p.bin_off[6], sm.w[0].rowsum);
+    bin_groups<32, T, G, EPI, HOT>(p, io, resid, dang, p.bin_off[4], p.bin_off[5]);
+    bin_groups<16, T, G, EPI, HOT>(p, io, resid, dang, p.bin_off[3], p.bin_off[4]);
+    bin_groups<8, T, G, EPI, HOT>(p, io, resid, dang, p.bin_off[2], p.bin_off[3]);
+    bin_groups<4, T, G, EPI, HOT>(p, io, resid, dang, p.bin_off[1], p.bin_off[2]);
+    bin_groups<1, T, G, EPI, HOT>(p, io, resid, dang, p.bin_off[0], p.bin_off[1]);
+    empty_rows<T, G, false, EPI, 4>(p, io, resid, dang);
+}
+
 // ------------------------------------------------ bulk-copy staging of tiles
 // The persistent loop can stream the per-tile arrays (256 column indices and
 // the 8 row-end words of a tile, 1056 bytes) into shared memory with
@@ -837,7 +934,7 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 // L1/L2; the copy costs hot_n words per CTA per body from L2.
 static_assert(sizeof(Smem<float, PR_HOT_BLOCK / 32>) <= PR_HOT_STATIC_SMEM, "static shared memory bound");
 
-template <class T, class G, int BLK, bool HOT, int NST = 0, bool PERS = false>
+template <class T, class G, int BLK, bool HOT, int NST = 0, bool PERS = false, bool BINS = false>
 __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS))
     pr_persistent_kernel(const __grid_constant__ PrParams p) {
     constexpr int EPI = PERS ? EPI_PERS : EPI_LEAN;
@@ -902,14 +999,18 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
             __syncthreads();
         }
         Acc<T> racc, dacc;
-        if constexpr (NST > 0)
-            phase_a_tma<T, G, G_W, EPI, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
-        else if constexpr (HOT)
-            phase_a_pipe<T, G, G_W, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
-        else
-            phase_a<T, G, G_W, false, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
-        if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
-        fixups<T, G, false, EPI>(p, io, racc, dacc);
+        if constexpr (BINS) {
+            phase_bins<T, G, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);   // no split rows: no phase B
+        } else {
+            if constexpr (NST > 0)
+                phase_a_tma<T, G, G_W, EPI, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
+            else if constexpr (HOT)
+                phase_a_pipe<T, G, G_W, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
+            else
+                phase_a<T, G, G_W, false, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
+            if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
+            fixups<T, G, false, EPI>(p, io, racc, dacc);
+        }
         const double resid = block_sum_d<BLK>(racc.value(), sm.red);
         dang = block_sum_d<BLK>(dacc.value(), sm.red2);
         double* part = p.part + 2 * G_ * ((it + 1) & 1);
@@ -1179,10 +1280,12 @@ void* pick_kernel(int32_t rank_type, int32_t gather_type, int32_t gmode, int per
 // The persistent loop with the shared-memory copy of the hottest gathered
 // entries: FP32 ranks and gathers only (the FP64 kernel's row-sum slices for
 // PR_HOT_BLOCK / 32 warps would exceed the static shared-memory limit).
-void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn, int32_t nst) {
+void* pick_hot(int32_t rank_type, int32_t gather_type, size_t dyn, int32_t nst, bool bins = false) {
     if (rank_type != GRB_FP32 || gather_type != GRB_FP32) return nullptr;
     void* k = nullptr;
+    if (bins) nst = -1;
     switch (nst) {
+        case -1: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 0, false, true>; break;
         case 0: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 0>; break;
         case 2: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 2>; break;
         case 3: k = (void*)pr_persistent_kernel<float, float, PR_HOT_BLOCK, true, 3>; break;
@@ -1275,14 +1378,18 @@ size_t pr_hot_dynamic_smem(int32_t hot_n, int32_t tma_stages) {
 }
 
 int pr_blocks_per_sm(int32_t rank_type, int32_t gather_type, int32_t gmode, int persistent, int32_t hot_n,
-                     int32_t tma_stages) {
+                     int32_t tma_stages, bool bins) {
     int block = PR_BLOCK;
     size_t dyn = 0;
     void* k = nullptr;
     if (persistent == 1 && hot_n > 0) {
-        dyn = pr_hot_dynamic_smem(hot_n, tma_stages);
+        dyn = pr_hot_dynamic_smem(hot_n, bins ? 0 : tma_stages);
         block = PR_HOT_BLOCK;
-        k = pick_hot(rank_type, gather_type, dyn, tma_stages);
+        k = pick_hot(rank_type, gather_type, dyn, tma_stages, bins);
+    } else if (persistent == 1 && bins) {
+        k = rank_type == GRB_FP32 && gather_type == GRB_FP32
+                ? (void*)pr_persistent_kernel<float, float, PR_BLOCK, false, 0, false, true>
+                : nullptr;
     } else {
         k = pick_kernel(rank_type, gather_type, gmode, persistent == 1, persistent == 2);
     }
@@ -1297,10 +1404,14 @@ cudaError_t launch_pr(cudaStream_t st, const PrParams& p, int32_t rank_type, int
     // persistent: 0 = one body (planner), 1 = whole loop, 2 = body of an
     // iterated sequence
     const bool hot = persistent == 1 && p.hot_n > 0;
+    const bool bins = persistent == 1 && p.bin_rows;
     if (hot && (p.hot_n % 4 != 0 || p.hot_n > p.nrows || p.mixed)) return cudaErrorInvalidValue;
-    const size_t dyn = hot ? pr_hot_dynamic_smem(p.hot_n, p.tma_stages) : 0;
-    void* k = hot ? pick_hot(rank_type, gather_type, dyn, p.tma_stages)
-                  : pick_kernel(rank_type, gather_type, p.gmode, persistent == 1, persistent == 2);
+    if (bins && (p.mixed || p.tma_stages || rank_type != GRB_FP32 || gather_type != GRB_FP32))
+        return cudaErrorInvalidValue;
+    const size_t dyn = hot ? pr_hot_dynamic_smem(p.hot_n, bins ? 0 : p.tma_stages) : 0;
+    void* k = hot ? pick_hot(rank_type, gather_type, dyn, p.tma_stages, bins)
+            : bins ? (void*)pr_persistent_kernel<float, float, PR_BLOCK, false, 0, false, true>
+                   : pick_kernel(rank_type, gather_type, p.gmode, persistent == 1, persistent == 2);
     if (!k) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);

@@ -28,7 +28,7 @@ def grb():
 
 
 def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, persistent=0, fusion=True,
-         mixed=False, relabel=True, hot_bytes=None, tma=0):
+         mixed=False, relabel=True, hot_bytes=None, tma=0, bins=False):
     from paper_2509_14211_gb300.pagerank import pagerank
 
     ctx = grb.grb_context_new(mode if mode is not None else grb.GRB_NONBLOCKING)
@@ -39,6 +39,7 @@ def _run(grb, n, src, dst, rank_type, dangling, loop, tol, itermax, mode=None, p
     if hot_bytes is not None:
         grb.grb_context_set(ctx, grb.GRB_OPT_HOT_BYTES, hot_bytes)
     grb.grb_context_set(ctx, grb.GRB_OPT_TMA_STAGES, tma)
+    grb.grb_context_set(ctx, grb.GRB_OPT_ROW_BINS, 1 if bins else 0)
     try:
         r, it = pagerank(ctx, n, src, dst, damping=D, tol=tol, itermax=itermax, rank_type=rank_type,
                          dangling=dangling, loop=loop)
@@ -91,12 +92,14 @@ def test_fp32_fixed_iterations_scale16(grb, dangling):
     # largest shared-memory hot copy (n = 65536: the largest covers 3/4 of
     # the vertices); the CUDA-graph loop; both on the input vertex order
     # and the tile arrays staged by bulk copies 2 and 3 tiles ahead
-    for persistent, relabel, hot, tma in ((1, True, None, 0), (1, True, 0, 0), (1, True, 1040, 0),
-                                          (1, True, grb.GRB_HOT_BYTES_MAX, 0), (2, True, None, 0),
-                                          (1, False, None, 0), (2, False, None, 0), (1, True, None, 2),
-                                          (1, True, None, 3), (1, True, 1040, 3)):
+    # and the row-length-binned body with and without the hot copy
+    for persistent, relabel, hot, tma, bins in ((1, True, None, 0, 0), (1, True, 0, 0, 0), (1, True, 1040, 0, 0),
+                                                (1, True, grb.GRB_HOT_BYTES_MAX, 0, 0), (2, True, None, 0, 0),
+                                                (1, False, None, 0, 0), (2, False, None, 0, 0), (1, True, None, 2, 0),
+                                                (1, True, None, 3, 0), (1, True, 1040, 3, 0), (1, True, None, 0, 1),
+                                                (1, True, 0, 0, 1), (1, False, None, 0, 1), (1, True, 1040, 0, 1)):
         r, it, _, (hist, _) = _run(grb, n, src, dst, grb.GRB_FP32, dangling, "device", -1.0, 50,
-                                   persistent=persistent, relabel=relabel, hot_bytes=hot, tma=tma)
+                                   persistent=persistent, relabel=relabel, hot_bytes=hot, tma=tma, bins=bins)
         assert it == 50
         assert np.sum(np.abs(r - ref)) <= 1e-6
         # FP32 ranks put a noise floor of ~n * eps32 * mean(r) ~ 1e-8 under
@@ -112,8 +115,9 @@ def test_fp32_full_size_rmat22(grb):
     n = 1 << 22
     src, dst = graphgen.rmat_edges(22, 16, seed=1)
     ref, k, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=50, mode="uniform")
-    for tma in (0, 2):
-        r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", -1.0, 50, persistent=1, tma=tma)
+    for tma, bins in ((0, False), (2, False), (0, True)):
+        r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP32, "uniform", "device", -1.0, 50, persistent=1, tma=tma,
+                           bins=bins)
         assert it == 50 == k
         assert np.sum(np.abs(r - ref)) <= 1e-6
     assert abs(np.sum(r) - 1.0) < 1e-4 and np.all(r >= 0)
@@ -237,8 +241,10 @@ def test_edge_graphs(grb, case):
         dst = (rng.integers(0, n // 7, 40000) * 7).astype(np.int32)
     for rank_type, tol_ok in ((grb.GRB_FP64, 1e-12), (grb.GRB_FP32, 1e-6)):
         ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=15, mode="uniform")
-        for loop, relabel in (("device", True), ("device", False), ("host", True)):
-            r, it, _, _ = _run(grb, n, src, dst, rank_type, "uniform", loop, -1.0, 15, relabel=relabel)
+        for loop, relabel, bins in (("device", True, False), ("device", False, False), ("host", True, False),
+                                    ("device", True, True), ("device", False, True)):
+            r, it, _, _ = _run(grb, n, src, dst, rank_type, "uniform", loop, -1.0, 15, relabel=relabel,
+                               persistent=1 if loop == "device" else 0, bins=bins)
             assert it == 15
             err = np.max(np.abs(r - ref)) if rank_type == grb.GRB_FP64 else np.sum(np.abs(r - ref))
             assert err <= tol_ok, (case, loop, err)

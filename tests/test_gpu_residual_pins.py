@@ -56,7 +56,7 @@ def _teleport(n, dmass):
     return np.float32(np.float64(np.float64(dmass * (D / n)) + (1.0 - D) / n))
 
 
-def _pin(grb, n, src, dst, ks, persistent, relabel, loop="device"):
+def _pin(grb, n, src, dst, ks, persistent, relabel, loop="device", bins=False):
     from paper_2509_14211_gb300.pagerank import PageRankProblem, build_graph
 
     outdeg, indeg = _degrees(n, src, dst)
@@ -66,6 +66,7 @@ def _pin(grb, n, src, dst, ks, persistent, relabel, loop="device"):
     try:
         grb.grb_context_set(ctx, grb.GRB_OPT_PERSISTENT, persistent)
         grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 1 if relabel else 0)
+        grb.grb_context_set(ctx, grb.GRB_OPT_ROW_BINS, 1 if bins else 0)
         AT = build_graph(ctx, n, src, dst)
         P = PageRankProblem(ctx, AT, n, D, grb.GRB_FP32, grb.GRB_FP64, "uniform")
         for k in ks:
@@ -93,17 +94,18 @@ def _pin(grb, n, src, dst, ks, persistent, relabel, loop="device"):
         grb.grb_free(ctx)
 
 
-# (persistent option, degree-ordered copy): the persistent kernel with the
-# shared-memory hot copy, the persistent kernel on the input vertex order,
-# the CUDA-graph loop of one fused kernel per body
-PATHS = [(1, True), (1, False), (2, True)]
+# (persistent option, degree-ordered copy, row-length bins): the persistent
+# kernel with the shared-memory hot copy, the persistent kernel on the input
+# vertex order, the CUDA-graph loop of one fused kernel per body, the binned
+# body
+PATHS = [(1, True, False), (1, False, False), (2, True, False), (1, True, True)]
 
 
-@pytest.mark.parametrize("persistent,relabel", PATHS)
-def test_residual_and_dangling_mass_rmat16(grb, persistent, relabel):
+@pytest.mark.parametrize("persistent,relabel,bins", PATHS)
+def test_residual_and_dangling_mass_rmat16(grb, persistent, relabel, bins):
     n = 1 << 16
     src, dst = graphgen.rmat_edges(16, 16, seed=1)
-    _pin(grb, n, src, dst, (2, 5, 30), persistent, relabel)
+    _pin(grb, n, src, dst, (2, 5, 30), persistent, relabel, bins=bins)
 
 
 def test_residual_host_loop_rmat16(grb):
