@@ -223,6 +223,37 @@ def test_deterministic_and_resumable(grb):
         grb.grb_free(ctx)
 
 
+def test_fixed_count_loops_are_enqueued_back_to_back(grb):
+    """Fixed-count device loops return without waiting: three loops enqueued
+    back to back (the rank vector rebuilt between them) end with the same
+    ranks and history as one loop run alone, and the device times of all
+    three are reported."""
+    from paper_2509_14211_gb300.pagerank import PageRankProblem, build_graph
+
+    n = 1 << 14
+    src, dst = graphgen.rmat_edges(14, 16, seed=8)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    try:
+        AT = build_graph(ctx, n, src, dst)
+        P = PageRankProblem(ctx, AT, n, D, grb.GRB_FP32)
+        assert P.run(-1.0, 20) == 20
+        alone = P.rank().copy()
+        hist_alone, _ = grb.grb_iterate_history(ctx)
+        for _ in range(3):
+            assert P.run(-1.0, 20) == 20
+        assert np.array_equal(P.rank(), alone)
+        hist, _ = grb.grb_iterate_history(ctx)
+        assert np.array_equal(hist, hist_alone) and len(hist) == 20
+        times = grb.grb_context_loop_times(ctx, 3)
+        assert len(times) == 3 and np.all(times > 0)
+        ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=20, mode="uniform")
+        assert np.sum(np.abs(alone.astype(np.float64) - ref)) <= 1e-6
+        P.free()
+        grb.grb_free(AT)
+    finally:
+        grb.grb_free(ctx)
+
+
 @pytest.mark.parametrize("case", ["single_vertex", "edgeless", "hub", "ragged"])
 def test_edge_graphs(grb, case):
     if case == "single_vertex":

@@ -121,6 +121,34 @@ def test_single_vector_loop_matches_slots_and_oracle(grb, setup):
             assert np.sum(np.abs(one["ranks"][q].astype(np.float64) - slot["ranks"][q])) <= 1e-6, q
 
 
+def test_single_vector_loop_on_the_input_vertex_order(grb):
+    """The single-vector loop on a context without the degree-ordered copy
+    (GRB_OPT_RELABEL 0: the personalised kernel without the hot copy) gives
+    the oracle's ranks at its body count."""
+    from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
+
+    n = 1 << 12
+    src, dst = graphgen.rmat_edges(12, 16, seed=6)
+    ctx = grb.grb_context_new(grb.GRB_NONBLOCKING)
+    grb.grb_context_set(ctx, grb.GRB_OPT_RELABEL, 0)
+    AT = grb.grb_matrix_build_csr(ctx, grb.GRB_FP32, n, n, src, dst, None, BUILD_FLAGS)
+    try:
+        sets = graphgen.ppr_seed_sets(n, 3, 1, 16, seed=16)
+        out = grb.grb_ppr_serve(AT, np.zeros(3), sets, damping=D, tol=1e-7, itermax=300, chunk=4, slots=32,
+                                want_ranks=True, single_max=8)
+        assert out["single_queries"] == 3
+        ptr, col = oracle.build_at(n, src, dst)
+        od = oracle.out_degree(ptr, col)
+        for q in range(3):
+            S = np.unique(sets[q])
+            ref, _, _ = oracle.pagerank(ptr, col, od, damping=D, tol=-1.0, itermax=int(out["iters"][q]),
+                                        mode="uniform", personal=SparseVec(n, S, np.full(len(S), 1.0 / len(S))))
+            assert np.sum(np.abs(out["ranks"][q].astype(np.float64) - ref)) <= 1e-6, q
+    finally:
+        grb.grb_free(AT)
+        grb.grb_free(ctx)
+
+
 def test_low_load_runs_single_then_batches_a_burst(grb, setup):
     """single_max = 2: queries spread out in time are answered alone on the
     single-vector loop; a burst of 40 arrivals goes to the slots."""
