@@ -462,9 +462,9 @@ def run_batch_leg(grb, torch, stream):
 def run_serve_leg(grb):
     """Serving: R-MAT scale 24 resident on the device, Poisson query streams
     (seed 4) with 1-64 log-uniform seeds, FP32 ranks with FP64 residual to an
-    L1 change of 1e-6, continuous batching in up to 128 slots; while no slot
-    is busy and at most 2 queries wait, a query runs alone on the fused
-    single-vector loop."""
+    L1 change of 1e-6, continuous batching in 64 slots with one body per
+    scheduling step; while no slot is busy and at most 2 queries wait, a
+    query runs alone on the fused single-vector loop."""
     import graphgen
     from paper_2509_14211_gb300.pagerank import BUILD_FLAGS
 
@@ -475,13 +475,13 @@ def run_serve_leg(grb):
     del src, dst
     m = grb.grb_matrix_nvals(AT)
     out = {"workload": "R-MAT scale 24 (16,777,216 vertices, edge factor 16, seed 4); queries with 1-64 log-uniform "
-                       "seeds; stop at L1 change 1e-6; chunk of 4 bodies per scheduling step; single-vector loop "
+                       "seeds; stop at L1 change 1e-6; 64 slots; one body per scheduling step; single-vector loop "
                        "while no slot is busy and at most 2 queries wait",
            "n": n, "m": m, "levels": []}
     for rate, count in ((10.0, 24), (200.0, 600), (1000.0, 1000), (2000.0, 1000)):
         sets = graphgen.ppr_seed_sets(n, count, 1, 64, seed=4, log_uniform=True)
         arr = graphgen.poisson_arrivals(rate, count, seed=4)
-        r = grb.grb_ppr_serve(AT, arr, sets, damping=DAMPING, tol=1e-6, itermax=1000, chunk=4, slots=0,
+        r = grb.grb_ppr_serve(AT, arr, sets, damping=DAMPING, tol=1e-6, itermax=1000, chunk=1, slots=64,
                               mem_fraction=0.5, single_max=2)
         lat = r["latency_s"]
         q = max(count // 4, 1)

@@ -28,6 +28,8 @@
 #include <chrono>
 #include <climits>
 #include <cstring>
+#include <functional>
+#include <queue>
 #include <thread>
 #include <vector>
 
@@ -246,10 +248,14 @@ grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, c
     out->single_queries = 0;
     SingleLoop one;
     if (cfg->single_max > 0) st = one.setup(A->ctx, A, cfg->damping, cfg->itermax);
-    std::vector<int32_t> slot_q(S, -1), free_slots, active(GRB_PPR_MAX_SLOTS);
+    std::vector<int32_t> slot_q(S, -1), active(GRB_PPR_MAX_SLOTS);
     std::vector<int64_t> its(GRB_PPR_MAX_SLOTS);
     std::vector<double> res(GRB_PPR_MAX_SLOTS);
-    for (int32_t s = S - 1; s >= 0; --s) free_slots.push_back(s);
+    // the lowest free slot first: queries pack into the low k-tiles, and a
+    // k-tile with no active slot is skipped by the body, so a higher k-tile
+    // runs only while more queries are in flight than the lower ones hold
+    std::priority_queue<int32_t, std::vector<int32_t>, std::greater<int32_t>> free_slots;
+    for (int32_t s = 0; s < S; ++s) free_slots.push(s);
     // bytes the slot buffers hold (already allocated): free memory is read
     // again at every admission and counted together with them
     const double pool_b = per_slot * (double)S;
@@ -295,8 +301,8 @@ grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, c
             usable = std::max<int64_t>(usable, 1);
         }
         while (next < nq && arrival_s[next] <= t && !free_slots.empty() && in_flight < usable) {
-            const int32_t s = free_slots.back();
-            free_slots.pop_back();
+            const int32_t s = free_slots.top();
+            free_slots.pop();
             st = grb_ppr_set(P, s, seed_idx + seed_ptr[next], seed_ptr[next + 1] - seed_ptr[next], cfg->tol,
                              cfg->itermax);
             if (st) break;
@@ -327,7 +333,7 @@ grb_info grb_ppr_serve(grb_matrix AT, const grb_serve_config* cfg, int64_t nq, c
             out->resid[q] = res[s];
             if (out->ranks) st = grb_ppr_get(P, s, out->ranks + (size_t)q * (size_t)n, 0);
             slot_q[s] = -1;
-            free_slots.push_back(s);
+            free_slots.push(s);
             --in_flight;
             ++done;
         }
