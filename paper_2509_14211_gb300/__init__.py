@@ -21,7 +21,10 @@ import numpy as np
 __all__ = [n for n in dir() if n.startswith("grb_") or n.startswith("GRB_")]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgrb.so")
+# GRB_CHECK_BOUNDS=1 in the environment selects the bounds-checked debug
+# build of the same library (include/grb_debug.h)
+CHECKED = os.environ.get("GRB_CHECK_BOUNDS", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "libgrb_checked.so" if CHECKED else "libgrb.so")
 
 # ---------------------------------------------------------------- constants
 GRB_SUCCESS, GRB_NO_VALUE = 0, 1
@@ -150,6 +153,10 @@ def _declare(lib):
         "grb_prbatch_run": [V, D, I64, I64],
         "grb_prbatch_result": [V, V, V, V],
     }
+    if CHECKED:
+        # include/grb_debug.h: exported by the bounds-checked build only
+        sig["grb_debug_check_csr"] = [V, V, V, U64, U64, U64, P(ctypes.c_int32), P(I64)]
+        sig["grb_debug_set_col"] = [V, U64, ctypes.c_int32]
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
@@ -157,7 +164,8 @@ def _declare(lib):
 
 
 def load():
-    """Load libgrb.so (raises if it was not built)."""
+    """Load libgrb.so, or libgrb_checked.so under GRB_CHECK_BOUNDS=1 (raises
+    if it was not built)."""
     global _lib
     with _lock:
         if _lib is None:
@@ -642,6 +650,24 @@ def grb_reduce_dense_noalloc(x, type_: int, n: int, monoid: int, out, stream=Non
 def grb_selftest_wait_timeout(ctx, spin_limit: int) -> int:
     """Returns the grb_info code (GRB_DEVICE_TIMEOUT expected)."""
     return load().grb_selftest_wait_timeout(ctx, int(spin_limit))
+
+
+def grb_debug_check_csr(ctx, row_ptr, col_idx, ncols: int):
+    """Bounds-checked build only: the device structure check on host CSR
+    arrays.  Returns (grb_info code, what, value) -- what 1: a column index
+    outside [0, ncols) (value = the index), 2: a row_ptr entry out of order
+    or outside [0, nnz] (value = its row)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    what, value = ctypes.c_int32(0), ctypes.c_int64(0)
+    rc = load().grb_debug_check_csr(ctx, rp.ctypes.data, ci.ctypes.data if ci.size else None, rp.size - 1,
+                                    int(ncols), ci.size, ctypes.byref(what), ctypes.byref(value))
+    return rc, what.value, value.value
+
+
+def grb_debug_set_col(A, k: int, col: int) -> None:
+    """Bounds-checked build only: overwrite column index k of A (no check)."""
+    _check(load().grb_debug_set_col(A, int(k), int(col)), "grb_debug_set_col", A)
 
 
 __all__ = [n for n in list(globals()) if n.startswith("grb_") or n.startswith("GRB_")] + \

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "grb_core.h"
+#include "grb_debug.h"
 
 using namespace grb;
 
@@ -227,9 +228,9 @@ grb_info grb_context_new(grb_context* ctx, grb_mode mode, void* cuda_stream, grb
     c->l2_bytes = (size_t)l2;
     const char* f = std::getenv("GRB_FUSION");
     if (f && f[0] == '0') c->fusion = false;
-    c->status = buf_alloc(c, sizeof(int32_t));
+    c->status = buf_alloc(c, STATUS_BYTES);
     c->sync = buf_alloc(c, sizeof(SyncWords));
-    if (!c->status.p || !c->sync.p || cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->stream) != cudaSuccess ||
+    if (!c->status.p || !c->sync.p || cudaMemsetAsync(c->status.p, 0, STATUS_BYTES, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->sync.p, 0, sizeof(SyncWords), c->stream) != cudaSuccess) {
         cudaGetLastError();
         buf_free(c, c->status);
@@ -994,5 +995,63 @@ grb_info grb_selftest_wait_timeout(grb_context ctx, int64_t spin_limit) {
     buf_free(c, sync);
     return st;
 }
+
+#ifdef GRB_CHECK_BOUNDS
+grb_info grb_debug_check_csr(grb_context ctx, const int32_t* row_ptr, const int32_t* col_idx, uint64_t nrows,
+                             uint64_t ncols, uint64_t nnz, int32_t* what, int64_t* value) {
+    Ctx* c = as_ctx(ctx);
+    if (!ctx || !row_ptr || !what || !value || (nnz > 0 && !col_idx)) return GRB_NULL_POINTER;
+    if (!c) return GRB_UNINITIALIZED_OBJECT;
+    if (nrows > (uint64_t)INT32_MAX || ncols > (uint64_t)INT32_MAX || nnz > (uint64_t)INT32_MAX)
+        return GRB_INVALID_VALUE;
+    *what = 0;
+    *value = 0;
+    grb_info st = read_status(c);   // nothing left over from earlier work
+    if (st) return st;
+    DevBuf rp = buf_alloc(c, sizeof(int32_t) * (size_t)(nrows + 1));
+    DevBuf ci = buf_alloc(c, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!rp.p || !ci.p) st = GRB_OUT_OF_MEMORY;
+    if (!st)
+        st = cuda_check(c, cudaMemcpyAsync(rp.p, row_ptr, sizeof(int32_t) * (size_t)(nrows + 1),
+                                           cudaMemcpyHostToDevice, c->stream), "check csr");
+    if (!st && nnz > 0)
+        st = cuda_check(c, cudaMemcpyAsync(ci.p, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice,
+                                           c->stream), "check csr");
+    if (!st) {
+        c->stats.kernel_launches++;
+        st = cuda_check(c, launch_csr_check(c->stream, (int64_t)nrows, (int64_t)ncols, (int64_t)nnz,
+                                            (const int32_t*)rp.p, (const int32_t*)ci.p, (int32_t*)c->status.p),
+                        "check csr");
+    }
+    int32_t w[4] = {0, 0, 0, 0};
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(w, c->status.p, STATUS_BYTES, cudaMemcpyDeviceToHost, c->stream),
+                             "check csr");
+    if (!st) st = cuda_check(c, cudaMemsetAsync(c->status.p, 0, STATUS_BYTES, c->stream), "check csr");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "check csr");
+    buf_free(c, rp);
+    buf_free(c, ci);
+    if (st) return st;
+    if (w[0] == 0) return GRB_SUCCESS;
+    *what = w[1];
+    long long v = 0;
+    std::memcpy(&v, w + 2, sizeof(v));
+    *value = (int64_t)v;
+    return (grb_info)w[0];
+}
+
+grb_info grb_debug_set_col(grb_matrix A, uint64_t k, int32_t col) {
+    Matrix* M = as_mat(A);
+    if (!A) return GRB_NULL_POINTER;
+    if (!M) return GRB_UNINITIALIZED_OBJECT;
+    if (k >= (uint64_t)M->nnz) return GRB_INVALID_INDEX;
+    Ctx* c = M->ctx;
+    grb_info st = cuda_check(c, cudaStreamSynchronize(c->stream), "set col");
+    if (!st)
+        st = cuda_check(c, cudaMemcpyAsync((int32_t*)M->col_idx.p + k, &col, sizeof(int32_t), cudaMemcpyHostToDevice,
+                                           c->stream), "set col");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "set col");
+    return st;
+}
+#endif
 
 }  // extern "C"

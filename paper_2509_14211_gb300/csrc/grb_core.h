@@ -131,6 +131,7 @@ struct Matrix {
     DevBuf new2old, old2new;
     uint64_t rel_id = 0;       // unique id of this relabelling
     bool rel_checked = false;  // the degree order was examined (rel null: not worth it)
+    bool structure_checked = false;  // bounds-checked builds: row_ptr / col_idx validated on the device
     std::string err;
 };
 
@@ -197,7 +198,7 @@ struct Ctx {
     grb_stats stats{};
     bool recording = false;
     std::vector<Stmt> body;
-    DevBuf status;        // int32 device status word (bounded waits)
+    DevBuf status;        // device status words (bounded waits, bounds checks), STATUS_BYTES
     DevBuf sync;          // grid-barrier words (SyncWords) of every launch on the stream; cleared with the
                           // status word after a device error
     cudaStream_t capture_stream = nullptr;   // CUDA-graph capture of device loops
@@ -260,6 +261,7 @@ grb_info iterate_end(Ctx* c, ScalarH* cond, double tol, int64_t itermax, int64_t
 VIn vin_of(const Version* v);
 size_t type_size(grb_type t);
 grb_info cuda_check(Ctx* c, cudaError_t e, const char* what);
+grb_info check_structure(Ctx* c, Matrix* A);
 grb_info ensure_plan(Ctx* c, Matrix* A);
 grb_info ensure_bins(Ctx* c, Matrix* A);
 grb_info ensure_sinkbits(Ctx* c, Version* sinks);

@@ -11,6 +11,32 @@
 
 namespace grb {
 
+// Bounds-checked builds (-DGRB_CHECK_BOUNDS, libgrb_checked.so): an index
+// read from a matrix's structure is tested against the extent of the array it
+// addresses before it is used; a bad one is replaced by 0 (in bounds of any
+// non-empty array) and the first failure is recorded in the context's status
+// words -- word 0 the code, word 1 what was checked, words 2-3 the offending
+// value as an int64 -- which the host reads at its next wait.  Release builds
+// compile the test away.
+
+__device__ __forceinline__ void bounds_record(int32_t* status, int32_t what, long long value) {
+    if (status && atomicCAS(status, 0, (int32_t)GRB_INDEX_OUT_OF_BOUNDS) == 0) {
+        status[1] = what;
+        *reinterpret_cast<long long*>(status + 2) = value;
+    }
+}
+
+#ifdef GRB_CHECK_BOUNDS
+static __device__ __noinline__ int bounds_fail(int32_t* status, int32_t what, long long value) {
+    bounds_record(status, what, value);
+    return 0;
+}
+#define GRB_CHECKED(j, n, status, what) \
+    ((unsigned)(j) < (unsigned)(n) ? (int)(j) : ::grb::bounds_fail((status), (what), (long long)(j)))
+#else
+#define GRB_CHECKED(j, n, status, what) (j)
+#endif
+
 template <class C>
 __device__ __forceinline__ C load_as(const void* p, int32_t type, int64_t i) {
     switch (type) {

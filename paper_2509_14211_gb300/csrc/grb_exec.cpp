@@ -20,6 +20,7 @@
 // dependencies (an input of a group is the output of an earlier group's last
 // node, since inner nodes of a group feed only that group).
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <unordered_map>
 #include <unordered_set>
@@ -182,8 +183,32 @@ grb_info ensure_bins(Ctx* c, Matrix* A) {
     return st;
 }
 
+// Bounds-checked builds validate a matrix's structure on the device before
+// the first kernel that walks it (plan, column counts, relabelling, general
+// mxv); the host reads the verdict before anything indexes with it.
+grb_info check_structure(Ctx* c, Matrix* A) {
+#ifdef GRB_CHECK_BOUNDS
+    if (A->structure_checked) return GRB_SUCCESS;
+    c->stats.kernel_launches++;
+    grb_info st = cuda_check(c, launch_csr_check(c->stream, A->nrows, A->ncols, A->nnz,
+                                                 (const int32_t*)A->row_ptr.p, (const int32_t*)A->col_idx.p,
+                                                 (int32_t*)c->status.p), "structure check");
+    if (!st) st = read_status(c);
+    if (!st) A->structure_checked = true;
+    return st;
+#else
+    (void)c;
+    (void)A;
+    return GRB_SUCCESS;
+#endif
+}
+
 grb_info ensure_plan(Ctx* c, Matrix* A) {
     if (A->plan) return GRB_SUCCESS;
+    {
+        const grb_info sc = check_structure(c, A);
+        if (sc) return sc;
+    }
     TilePlan* p = new TilePlan();
     p->ntiles = padded_nnz(A->nnz) / PR_NZTILE;
     const int64_t n = A->nrows;
@@ -247,6 +272,10 @@ static constexpr double REL_MIN_COVER = 0.10;
 
 grb_info ensure_coldeg(Ctx* c, Matrix* A) {
     if (A->coldeg.p) return GRB_SUCCESS;
+    {
+        const grb_info sc = check_structure(c, A);
+        if (sc) return sc;
+    }
     DevBuf d = buf_alloc(c, sizeof(int32_t) * (size_t)(A->ncols > 0 ? A->ncols : 1));
     if (!d.p) return GRB_OUT_OF_MEMORY;
     c->stats.kernel_launches++;
@@ -380,6 +409,7 @@ static PrParams plan_params(Ctx* c, Matrix* A) {
     p.col_idx = (const int32_t*)A->col_idx.p;
     p.nrows = (int32_t)A->nrows;
     p.nnz = (int32_t)A->nnz;
+    p.ncols = (int32_t)A->ncols;
     p.ntiles = (int32_t)pl->ntiles;
     p.tile_meta = (const uint32_t*)pl->meta.p;
     p.rowend_bits = (const uint32_t*)pl->rowend_bits.p;
@@ -417,17 +447,34 @@ int pr_grid(Ctx* c, Matrix* A, int32_t T, int32_t G, int32_t gmode, int persiste
 }
 
 grb_info read_status(Ctx* c) {
-    int32_t st = 0;
-    grb_info e = cuda_check(c, cudaMemcpyAsync(&st, c->status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream),
+    // word 0 the code; words 1-3 what a bounds check found (checked builds)
+    int32_t w[4] = {0, 0, 0, 0};
+    grb_info e = cuda_check(c, cudaMemcpyAsync(w, c->status.p, STATUS_BYTES, cudaMemcpyDeviceToHost, c->stream),
                             "status read");
     if (e) return e;
     e = cuda_check(c, cudaStreamSynchronize(c->stream), "stream sync");
     if (e) return e;
+    const int32_t st = w[0];
     if (st != 0) {
-        cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->stream);
+        cudaMemsetAsync(c->status.p, 0, STATUS_BYTES, c->stream);
         // a barrier that gave up leaves its counter mid-crossing
         cudaMemsetAsync(c->sync.p, 0, sizeof(SyncWords), c->stream);
-        c->err = st == (int32_t)GRB_DEVICE_TIMEOUT ? "a bounded device-side wait ran out" : "device status error";
+        if (st == (int32_t)GRB_DEVICE_TIMEOUT) {
+            c->err = "a bounded device-side wait ran out";
+        } else if (st == (int32_t)GRB_INDEX_OUT_OF_BOUNDS) {
+            long long v = 0;
+            std::memcpy(&v, w + 2, sizeof(v));
+            char msg[160];
+            if (w[1] == BOUNDS_ROW_PTR)
+                std::snprintf(msg, sizeof msg, "bounds check: row_ptr[%lld] out of order or outside [0, nnz]", v);
+            else if (w[1] == BOUNDS_COLUMN)
+                std::snprintf(msg, sizeof msg, "bounds check: column index %lld outside [0, ncols)", v);
+            else
+                std::snprintf(msg, sizeof msg, "bounds check: index %lld out of range", v);
+            c->err = msg;
+        } else {
+            c->err = "device status error";
+        }
         return (grb_info)st;
     }
     return GRB_SUCCESS;
@@ -549,10 +596,11 @@ static grb_info exec_mxv(Ctx* c, Node* nd, Version* out) {
     o.present = (uint8_t*)tmp.present.p;
     o.type = T;
     o.full = 0;
+    if ((st = check_structure(c, A))) { ver_free_data(&tmp); return st; }
     c->stats.kernel_launches += 2;
     st = cuda_check(c, launch_mxv_generic(c->stream, A->nrows, (const int32_t*)A->row_ptr.p,
                                           (const int32_t*)A->col_idx.p, A->vals.p, A->type, A->iso_val, vin_of(u),
-                                          add, mul, o), "mxv");
+                                          add, mul, o, A->ncols, (int32_t*)c->status.p), "mxv");
     if (!st) {
         Node cp;
         cp.k = OpK::APPLY;

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "grb.h"
@@ -136,11 +137,18 @@ struct MgFinish {
 //         = s_i, present iff row non-empty                        otherwise
 // plus optional epilogue outputs: w_next_i = out_i / dd_i, the residual
 // sum |r_old_i - out_i| and the dangling mass sum over sink rows of out_i.
+// The context's status words: int32 0 the code (a bounded wait that ran out,
+// a failed bounds check), int32 1 what a bounds check tested, int32 2-3 the
+// offending value as an int64.
+constexpr size_t STATUS_BYTES = 16;
+enum BoundsWhat : int32_t { BOUNDS_COLUMN = 1, BOUNDS_ROW_PTR = 2 };
+
 struct PrParams {
     // matrix and plan
     const int32_t* row_ptr = nullptr;
     const int32_t* col_idx = nullptr;   // padded to ntiles * PR_NZTILE
     int32_t nrows = 0, nnz = 0;
+    int32_t ncols = 0;                  // entries of the gathered vector (bounds-checked builds)
     int32_t ntiles = 0;
     const uint32_t* tile_meta = nullptr;  // first non-empty row of the tile | (continues a row) << 31
     const uint32_t* rowend_bits = nullptr;  // bit k: nonzero k is the last of its row
@@ -257,7 +265,7 @@ cudaError_t launch_build_sparse(cudaStream_t st, int64_t n, const int32_t* idx, 
 cudaError_t launch_sinkbits(cudaStream_t st, int64_t n, VIn v, uint32_t* bits);
 cudaError_t launch_mxv_generic(cudaStream_t st, int64_t nrows, const int32_t* row_ptr, const int32_t* col_idx,
                                const void* avals, int32_t a_type, double a_iso, VIn u, int32_t add_monoid,
-                               int32_t mul_op, VOut out);
+                               int32_t mul_op, VOut out, int64_t ncols, int32_t* status);
 
 // CSR build: returns the deduplicated nnz through *nnz_out (synchronises).
 struct CsrBuildArgs {
@@ -274,6 +282,11 @@ cudaError_t csr_build(cudaStream_t st, const CsrBuildArgs& a, AllocFn af, FreeFn
                       int32_t** row_ptr, int32_t** col_idx, void** vals_out, int64_t* nnz_out, int32_t* bad_index);
 // deg[j] = entries in column j
 cudaError_t launch_col_count(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx, int32_t* deg);
+// Structure check (bounds-checked builds, before a matrix's first use): the
+// first row_ptr entry out of order or outside [0, nnz], or column index
+// outside [0, ncols), goes to status (GRB_INDEX_OUT_OF_BOUNDS, what, value).
+cudaError_t launch_csr_check(cudaStream_t st, int64_t nrows, int64_t ncols, int64_t nnz, const int32_t* row_ptr,
+                             const int32_t* col_idx, int32_t* status);
 // present[j] = deg[j] > 0
 cudaError_t launch_deg_present(cudaStream_t st, int64_t ncols, const int32_t* deg, uint8_t* present);
 cudaError_t launch_col_degree(cudaStream_t st, int64_t ncols, int64_t nnz, const int32_t* col_idx,
@@ -376,6 +389,7 @@ struct PprParams {
     const int32_t* active = nullptr;    // kt*32
     const float* tele_base = nullptr;   // kt*32: damping * D_s / n
     double* part = nullptr;             // [grid][kt*32][2] residual, dangling mass
+    int32_t* status = nullptr;          // context status words (bounds-checked builds)
 };
 
 struct PprFinish {

@@ -118,6 +118,7 @@ PprParams params(Ppr* P, int from) {
     p.nrows = (int32_t)P->n;
     p.nnz = (int32_t)P->A->nnz;
     p.ntiles = (int32_t)pl->ntiles;
+    p.status = (int32_t*)P->c->status.p;
     p.tile_meta = (const uint32_t*)pl->meta.p;
     p.rowend_bits = (const uint32_t*)pl->rowend_bits.p;
     p.ne_rows = (const int32_t*)pl->ne_rows.p;
@@ -525,6 +526,9 @@ grb_info grb_ppr_status(grb_ppr Ph, int32_t* active, int64_t* iters, double* res
     if (!st) st = cuda_check(c, cudaMemcpyAsync(rs.data(), P->resid.p, 8 * S, cudaMemcpyDeviceToHost, c->stream),
                              "ppr status");
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "ppr status");
+#ifdef GRB_CHECK_BOUNDS
+    if (!st) st = read_status(c);   // a failed bounds check in the bodies run so far
+#endif
     if (st) return st;
     for (int s = 0; s < S; ++s) {
         if (active) active[s] = a[s];

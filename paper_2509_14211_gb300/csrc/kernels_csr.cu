@@ -83,6 +83,26 @@ __global__ void col_count_kernel(int64_t nnz, const int32_t* __restrict__ col_id
         atomicAdd(&deg[col_idx[p]], 1);
 }
 
+// Structure check of a CSR matrix: row_ptr starts at 0, ends at nnz and
+// never decreases; every column index lies in [0, ncols).  Reads only
+// row_ptr[0..nrows] and col_idx[0..nnz) -- no value read is used as an
+// address -- and records the first failure in the status words.
+__global__ void csr_check_kernel(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col_idx, int32_t* status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i <= nrows; i += stride) {
+        const int64_t a = row_ptr[i];
+        bool bad = a < 0 || a > nnz || (i == 0 && a != 0) || (i == nrows && a != nnz);
+        if (i < nrows && (int64_t)row_ptr[i + 1] < a) bad = true;
+        if (bad) bounds_record(status, BOUNDS_ROW_PTR, (long long)i);
+    }
+    for (int64_t k = t0; k < nnz; k += stride) {
+        const int64_t j = col_idx[k];
+        if (j < 0 || j >= ncols) bounds_record(status, BOUNDS_COLUMN, (long long)j);
+    }
+}
+
 __global__ void deg_present_kernel(int64_t n, const int32_t* deg, uint8_t* present) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         present[i] = deg[i] > 0 ? 1 : 0;
@@ -390,6 +410,13 @@ cudaError_t launch_col_count(cudaStream_t st, int64_t ncols, int64_t nnz, const 
     cudaError_t e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * (ncols > 0 ? ncols : 1), st);
     if (e != cudaSuccess) return e;
     if (nnz > 0) col_count_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, col_idx, deg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_check(cudaStream_t st, int64_t nrows, int64_t ncols, int64_t nnz, const int32_t* row_ptr,
+                             const int32_t* col_idx, int32_t* status) {
+    const int64_t work = nrows + 1 > nnz ? nrows + 1 : nnz;
+    csr_check_kernel<<<grid_for(work), 256, 0, st>>>(nrows, ncols, nnz, row_ptr, col_idx, status);
     return cudaGetLastError();
 }
 

@@ -179,7 +179,8 @@ __global__ void sinkbits_kernel(int64_t n, VIn v, uint32_t* bits) {
 template <class C>
 __global__ void mxv_generic_kernel(int64_t nrows, const int32_t* __restrict__ row_ptr,
                                    const int32_t* __restrict__ col_idx, const void* avals, int32_t a_type,
-                                   double a_iso, VIn u, int32_t add_mon, int32_t mul_op, VOut out) {
+                                   double a_iso, VIn u, int32_t add_mon, int32_t mul_op, VOut out,
+                                   int64_t ncols, int32_t* status) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); row < nrows; row += warps) {
@@ -188,7 +189,8 @@ __global__ void mxv_generic_kernel(int64_t nrows, const int32_t* __restrict__ ro
         bool found = false;
         for (int32_t p = b + lane; p < e; p += 32) {
             C x;
-            if (!vin_get<C>(u, col_idx[p], x)) continue;
+            const int32_t j = col_idx[p];
+            if (!vin_get<C>(u, GRB_CHECKED(j, ncols, status, BOUNDS_COLUMN), x)) continue;
             const C a = avals ? load_as<C>(avals, a_type, p) : (C)a_iso;
             acc = monoid_apply<C>(add_mon, acc, binop<C>(mul_op, 0.0, a, x));
             found = true;
@@ -266,15 +268,15 @@ cudaError_t launch_sinkbits(cudaStream_t st, int64_t n, VIn v, uint32_t* bits) {
 
 cudaError_t launch_mxv_generic(cudaStream_t st, int64_t nrows, const int32_t* row_ptr, const int32_t* col_idx,
                                const void* avals, int32_t a_type, double a_iso, VIn u, int32_t add_monoid,
-                               int32_t mul_op, VOut out) {
+                               int32_t mul_op, VOut out, int64_t ncols, int32_t* status) {
     if (nrows <= 0) return cudaSuccess;
     const int grid = grid_for(nrows * 32, 256);
     if (is_f32(out.type))
         mxv_generic_kernel<float><<<grid, 256, 0, st>>>(nrows, row_ptr, col_idx, avals, a_type, a_iso, u, add_monoid,
-                                                        mul_op, out);
+                                                        mul_op, out, ncols, status);
     else
         mxv_generic_kernel<double><<<grid, 256, 0, st>>>(nrows, row_ptr, col_idx, avals, a_type, a_iso, u, add_monoid,
-                                                         mul_op, out);
+                                                         mul_op, out, ncols, status);
     return cudaGetLastError();
 }
 

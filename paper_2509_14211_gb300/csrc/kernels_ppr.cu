@@ -328,6 +328,10 @@ __device__ __forceinline__ void ppr_tile(const PprParams& p, int kt, int t, int 
         c[5] = __shfl_sync(FULL, cb.y, src);
         c[6] = __shfl_sync(FULL, cb.z, src);
         c[7] = __shfl_sync(FULL, cb.w, src);
+#ifdef GRB_CHECK_BOUNDS
+#pragma unroll
+        for (int q = 0; q < PR_NZLANE; ++q) c[q] = GRB_CHECKED(c[q], p.nrows, p.status, BOUNDS_COLUMN);
+#endif
         const uint32_t f = __shfl_sync(FULL, myf, src);
 #pragma unroll
         for (int q0 = 0; q0 < PR_NZLANE; q0 += U) {

@@ -320,6 +320,7 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
 
 template <class T, class G, int GMODE, bool NC, bool HOT = false>
 __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, int j) {
+    j = GRB_CHECKED(j, p.ncols, p.status, BOUNDS_COLUMN);
     if constexpr (HOT) {
         // the hot copy in shared memory, or L2 (bypassing L1: the columns
         // past the copy are rarely reused soon enough for L1 to help); two

@@ -47,6 +47,28 @@ def test_binding_covers_every_declared_symbol(lib):
         assert callable(getattr(grb, n))
 
 
+def _declared_debug():
+    with open(os.path.join(ROOT, "include", "grb_debug.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^grb_info\s+(grb_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_checked_build_exports_the_debug_calls(lib):
+    """libgrb_checked.so (the same sources with -DGRB_CHECK_BOUNDS) exports
+    everything include/grb.h and include/grb_debug.h declare; the release
+    library exports none of the debug calls."""
+    import ctypes
+
+    from paper_2509_14211_gb300 import _build
+
+    debug = _declared_debug()
+    assert debug == ["grb_debug_check_csr", "grb_debug_set_col"]
+    checked = ctypes.CDLL(_build.LIB_CHECKED)
+    missing = [n for n in _declared() + debug if not hasattr(checked, n)]
+    assert not missing, missing
+    assert not [n for n in debug if hasattr(lib, n)]
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     import paper_2509_14211_gb300 as grb
 
