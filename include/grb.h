@@ -25,6 +25,10 @@
  *    runs -- at grb_wait or a call that forces it -- and stick to the output
  *    object; grb_error() returns the message.
  *  - Indices are 32-bit (§IV uses 32-bit indices): n < 2^31, nnz < 2^31.
+ *    The fused row-gather kernels (device loops, the fused mxv, grb_ppr_*,
+ *    grb_prbatch_*) take a matrix while nrows + nnz < 2^31 - 2^24
+ *    (GRB_FUSED_INDEX_LIMIT); past it, mxv and the loops run on the general
+ *    kernels, and grb_ppr_new / grb_prbatch_new return GRB_INVALID_VALUE.
  */
 #ifndef GRB_H
 #define GRB_H
@@ -151,6 +155,7 @@ typedef enum {
 } grb_option;
 
 #define GRB_HOT_BYTES_MAX 196608
+#define GRB_FUSED_INDEX_LIMIT 2130706432LL   /* 2^31 - 2^24: bound on nrows + nnz of the fused kernels */
 
 /* Opaque handles. */
 typedef struct grb_context_s* grb_context;
@@ -367,8 +372,9 @@ typedef struct grb_ppr_s* grb_ppr;
 /* New batch object with `slots` slots (rounded up to a multiple of 32;
  * grb_ppr_slots returns the count), all empty, vector width 1.  Device memory: about
  * 16 * n * slots bytes.  Errors: GRB_NULL_POINTER, GRB_UNINITIALIZED_OBJECT,
- * GRB_INVALID_VALUE (non-square or valued matrix, slots outside
- * 1..GRB_PPR_MAX_SLOTS, damping outside [0, 1)), GRB_OUT_OF_MEMORY. */
+ * GRB_INVALID_VALUE (non-square or valued matrix, nrows + nnz at or past
+ * GRB_FUSED_INDEX_LIMIT, slots outside 1..GRB_PPR_MAX_SLOTS, damping outside
+ * [0, 1)), GRB_OUT_OF_MEMORY. */
 grb_info grb_ppr_new(grb_ppr* P, grb_matrix AT, double damping, int32_t slots);
 grb_info grb_ppr_slots(grb_ppr P, int32_t* slots);
 
@@ -472,7 +478,8 @@ typedef struct grb_prbatch_s* grb_prbatch;
 /* vptr: host, ngraphs + 1 non-decreasing offsets with vptr[0] = 0,
  * vptr[ngraphs] = nrows(AT), every graph at least one vertex.  Holds a
  * reference to AT.  Errors: GRB_INVALID_VALUE (bad offsets, non-square or
- * valued matrix, an edge across graphs, damping outside [0, 1)). */
+ * valued matrix, nrows + nnz at or past GRB_FUSED_INDEX_LIMIT, an edge across
+ * graphs, damping outside [0, 1)). */
 grb_info grb_prbatch_new(grb_prbatch* B, grb_matrix AT, int32_t ngraphs, const int64_t* vptr, double damping);
 
 /* Autotune: time trial_bodies (1..1000) bodies for every candidate count of

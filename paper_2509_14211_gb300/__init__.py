@@ -50,6 +50,7 @@ GRB_OPT_HOT_BYTES = 7
 GRB_OPT_TMA_STAGES = 8
 GRB_OPT_ROW_BINS = 9
 GRB_HOT_BYTES_MAX = 196608
+GRB_FUSED_INDEX_LIMIT = 2130706432   # 2^31 - 2^24: nrows + nnz bound of the fused kernels
 
 NP_TYPES = {GRB_INT32: np.int32, GRB_FP32: np.float32, GRB_FP64: np.float64, GRB_BF16: np.uint16}
 

@@ -540,7 +540,7 @@ static bool mxv_fast_ok(const Node* nd, const Version* u, grb_type T) {
     if (A->vals.p) return false;
     if (!(nd->sr == GRB_PLUS_SECOND || (nd->sr == GRB_PLUS_TIMES && A->iso_val == 1.0))) return false;
     if (!(T == GRB_FP32 || T == GRB_FP64)) return false;
-    if (A->nrows + A->nnz >= ((int64_t)1 << 31)) return false;
+    if (A->nrows + A->nnz >= PR_INDEX_LIMIT) return false;
     if (nd->has_accum) {
         if (nd->accum.opcode != GRB_PLUS || !nd->w_old || nd->w_old->type != T) return false;
     }

@@ -158,7 +158,7 @@ bool match_body(Version* r0, Version* Vr, Version* Vc, LoopMatch& lm) {
     if (M->mask || A->vals.p || M->out->type != T) return false;
     if (!(M->sr == GRB_PLUS_SECOND || (M->sr == GRB_PLUS_TIMES && A->iso_val == 1.0))) return false;
     if (A->nrows != r0->n || A->ncols != r0->n) return false;
-    if (A->nrows + A->nnz >= ((int64_t)1 << 31)) return false;
+    if (A->nrows + A->nnz >= PR_INDEX_LIMIT) return false;
     Node* W = M->u->producer;
     if (!W || W->k != OpK::EMULT || W->op.opcode != GRB_DIV || W->mask || W->has_accum || W->u != r0) return false;
     if (W->out->type != T || !invariant_full(W->v, T, false)) return false;

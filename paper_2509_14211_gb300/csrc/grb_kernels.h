@@ -80,6 +80,15 @@ constexpr int PR_NZLANE = 8;
 constexpr int PR_NZTILE = 32 * PR_NZLANE;
 constexpr int PR_LONG = 8;   // split rows spanning more tiles are joined by a whole warp
 
+// The fused row-gather kernels (the PageRank, batched PPR and graph-batch
+// bodies and their row plan) index rows and nonzeros with int32, including
+// grid-stride steps (below 2^24) and row offsets within a tile; they take a
+// matrix only when nrows + nnz stays below this limit.  Larger matrices (up
+// to the CSR limit of 2^31 - 1 rows and nonzeros) run on the general kernels,
+// which index with int64.
+constexpr int64_t PR_INDEX_LIMIT = (int64_t(1) << 31) - (int64_t(1) << 24);
+static_assert(PR_INDEX_LIMIT == GRB_FUSED_INDEX_LIMIT, "the header states the same limit");
+
 // col_idx arrays are allocated to a whole number of tiles (padding = col 0).
 inline int64_t padded_nnz(int64_t nnz) {
     const int64_t t = (nnz > 0 ? nnz : 1) + PR_NZTILE - 1;

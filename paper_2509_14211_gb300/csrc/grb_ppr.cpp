@@ -332,7 +332,7 @@ grb_info grb_ppr_new(grb_ppr* out, grb_matrix Am, double damping, int32_t slots)
     Matrix* A = reinterpret_cast<Matrix*>(Am);
     if (A->kind != Kind::MATRIX) return GRB_UNINITIALIZED_OBJECT;
     if (A->nrows != A->ncols || A->vals.p) return GRB_INVALID_VALUE;      // square pattern A^T
-    if (A->nrows < 1 || A->nrows + A->nnz >= ((int64_t)1 << 31)) return GRB_INVALID_VALUE;
+    if (A->nrows < 1 || A->nrows + A->nnz >= PR_INDEX_LIMIT) return GRB_INVALID_VALUE;
     if (slots < 1 || slots > PPR_MAX_SLOTS || !(damping >= 0.0 && damping < 1.0)) return GRB_INVALID_VALUE;
     Ctx* c = A->ctx;
     grb_info st = ensure_plan(c, A);

@@ -220,7 +220,7 @@ grb_info grb_prbatch_new(grb_prbatch* out, grb_matrix Am, int32_t ngraphs, const
     *out = nullptr;
     Matrix* A = reinterpret_cast<Matrix*>(Am);
     if (A->kind != Kind::MATRIX) return GRB_UNINITIALIZED_OBJECT;
-    if (A->nrows != A->ncols || A->vals.p || A->nrows + A->nnz >= ((int64_t)1 << 31)) return GRB_INVALID_VALUE;
+    if (A->nrows != A->ncols || A->vals.p || A->nrows + A->nnz >= PR_INDEX_LIMIT) return GRB_INVALID_VALUE;
     if (ngraphs < 1 || !(damping >= 0.0 && damping < 1.0)) return GRB_INVALID_VALUE;
     if (vptr[0] != 0 || vptr[ngraphs] != A->nrows) return GRB_INVALID_VALUE;
     for (int32_t g = 0; g < ngraphs; ++g)

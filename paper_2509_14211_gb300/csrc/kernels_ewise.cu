@@ -187,7 +187,8 @@ __global__ void mxv_generic_kernel(int64_t nrows, const int32_t* __restrict__ ro
         const int32_t b = row_ptr[row], e = row_ptr[row + 1];
         C acc = (C)monoid_identity(add_mon);
         bool found = false;
-        for (int32_t p = b + lane; p < e; p += 32) {
+        // 64-bit: on a matrix with close to 2^31 nonzeros p + 32 passes INT32_MAX
+        for (int64_t p = (int64_t)b + lane; p < e; p += 32) {
             C x;
             const int32_t j = col_idx[p];
             if (!vin_get<C>(u, GRB_CHECKED(j, ncols, status, BOUNDS_COLUMN), x)) continue;
