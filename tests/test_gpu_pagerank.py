@@ -293,3 +293,39 @@ def test_loop_kernel_counts(grb, c0):
     assert sh["kernel_launches"] - sd["kernel_launches"] >= 2 * 30
     assert sb["kernel_launches"] > sh["kernel_launches"]
     assert sb["fused_groups"] == 0 and sh["fused_groups"] >= 30
+
+
+def _sink_free(case):
+    """Graphs in which every vertex has an out-edge: no dangling mass, the
+    sink vector of the program is empty."""
+    if case == "cycle":                      # one directed cycle: r stays 1/n
+        n = 7
+        src = np.arange(n, dtype=np.int32)
+        return n, src, ((src + 1) % n).astype(np.int32)
+    rng = np.random.default_rng(21)
+    n = 3000
+    # 3 distinct out-edges per vertex, none to itself; in-degrees vary (some
+    # vertices have none: rows without nonzeros)
+    offs = np.stack([1 + rng.choice(n - 1, 3, replace=False) for _ in range(n)])
+    src = np.repeat(np.arange(n), 3).astype(np.int32)
+    dst = ((src + offs.reshape(-1)) % n).astype(np.int32)
+    return n, src, dst
+
+
+@pytest.mark.parametrize("case", ["cycle", "out3"])
+@pytest.mark.parametrize("loop,persistent,fusion,mode,relabel", PATHS)
+def test_sink_free_graphs_all_paths(grb, case, loop, persistent, fusion, mode, relabel):
+    """A degenerate case of the method: no vertex without out-edges, so the
+    dangling-mass sum runs over an empty set.  FP64 ranks after 15 bodies
+    match the oracle within 1e-12 on every path, in both dangling modes (which
+    agree here); the cycle stays at 1/n exactly in exact arithmetic."""
+    n, src, dst = _sink_free(case)
+    for dangling in ("uniform", "gap"):
+        ref, _, _ = oracle.pagerank_edges(n, src, dst, damping=D, tol=-1.0, itermax=15, mode=dangling)
+        r, it, _, _ = _run(grb, n, src, dst, grb.GRB_FP64, dangling, loop, -1.0, 15,
+                           mode=grb.GRB_BLOCKING if mode == "blocking" else None, persistent=persistent,
+                           fusion=fusion, relabel=relabel)
+        assert it == 15
+        assert np.max(np.abs(r - ref)) <= 1e-12, (case, loop, persistent, dangling)
+        if case == "cycle":
+            assert np.max(np.abs(r - 1.0 / n)) <= 1e-15
