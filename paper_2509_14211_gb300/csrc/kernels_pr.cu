@@ -214,6 +214,7 @@ struct TileIO {
     int phase32;       // mixed precision: gather from w32
     const G* hot;      // shared-memory copy of w[0, hot_n) (HOT kernels)
     int hot_n;
+    uint32_t epoch;    // single-pass bodies: the body's tag on published tile carries
 };
 
 // Epilogue kinds: the general one (any fused group), the PageRank loop body
@@ -403,8 +404,31 @@ __device__ __forceinline__ TileVals<T, EPI> tile_issue(const PrParams& p, int t,
     return tv;
 }
 
+// A tile's carry (the part of the row open at its end).  In single-pass
+// bodies (LB) it is published as one 64-bit word {value, body tag}, so a
+// reader that sees the tag sees the value: no fence, no separate flag.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* a, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* a) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
+template <bool LB, class T, class G>
+__device__ __forceinline__ void store_carry(const PrParams& p, const TileIO<T, G>& io, int t, T val) {
+    if constexpr (LB && sizeof(T) == 4) {
+        st_relaxed_u64(reinterpret_cast<unsigned long long*>(p.agg) + t,
+                       ((unsigned long long)io.epoch << 32) | (unsigned long long)__float_as_uint((float)val));
+    } else {
+        reinterpret_cast<T*>(p.agg)[t] = val;
+    }
+}
+
 // Second half: row numbering, segmented sums, carries and the epilogue.
-template <class T, class G, bool NC, int EPI>
+template <class T, class G, bool NC, int EPI, bool LB = false>
 __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const TilePre& f, const TileVals<T, EPI>& tv,
                                             const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
                                             WarpSmem<T>& ws) {
@@ -438,7 +462,7 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
             const T v2 = __shfl_up_sync(FULLMASK, val, off);
             if (lane >= off) val = v2 + val;
         }
-        if (lane == 31) reinterpret_cast<T*>(p.agg)[t] = val;
+        if (lane == 31) store_carry<LB>(p, io, t, val);
         return;
     }
 
@@ -483,7 +507,7 @@ __device__ __forceinline__ void tile_finish(const PrParams& p, int t, const Tile
     // the carry of lanes below ends this lane's first row (row `before`)
     const T exv = __shfl_up_sync(FULLMASK, val, 1);
     if (lane > 0 && cnt > 0) ws.rowsum[before] = exv + ws.rowsum[before];
-    if (lane == 31) reinterpret_cast<T*>(p.agg)[t] = val;
+    if (lane == 31) store_carry<LB>(p, io, t, val);
     __syncwarp();
 
     // ---- epilogue of the rows finished here (row x on lane x % 32)
@@ -571,6 +595,72 @@ __device__ __forceinline__ void fixups(const PrParams& p, const TileIO<T, G>& io
     }
 }
 
+// Single-pass bodies: the rows split across tiles are finished by the warp
+// that finished the tile they end in, after its tile loop (by then the
+// carries of the tiles before them, finished by other warps, have almost
+// always been published), from the carries tagged with this body.  Each
+// lane takes one of the warp's tiles (short fixups, at most PR_LONG
+// carries, summed by the lane); fixups of longer rows take the whole warp.
+// The sums are those of phase B, in the same order: the same bits.  Every
+// wait is for a lower tile index, so the waits cannot form a cycle; each is
+// bounded.
+template <class T>
+__device__ __forceinline__ T carry_of(const PrParams& p, const unsigned long long* agg, int tt, uint32_t epoch,
+                                      bool& ok) {
+    for (int64_t spins = 0; ok; ++spins) {
+        const unsigned long long x = ld_relaxed_u64(agg + tt);
+        if ((uint32_t)(x >> 32) == epoch) return (T)__uint_as_float((uint32_t)x);
+        if (spins > p.spin_limit) ok = false;
+    }
+    return (T)0;
+}
+
+template <class T, class G, int EPI, int NW>
+__device__ __forceinline__ void lookback_fixups(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid,
+                                                Acc<T>& dang) {
+    static_assert(sizeof(T) == 4, "single-pass bodies publish FP32 carries");
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * NW + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * NW;
+    const unsigned long long* agg = reinterpret_cast<const unsigned long long*>(p.agg);
+    const T* first = reinterpret_cast<const T*>(p.first);
+    bool ok = true;
+    __syncwarp();   // first[] of this warp's tiles, written by lane 0, read by any lane
+    for (int64_t k0 = 0; w0 + k0 * nw < p.ntiles; k0 += 32) {
+        const int64_t tl = w0 + (k0 + lane) * nw;
+        int longt = -1;
+        if (tl < p.ntiles && (__ldg(p.tile_meta + tl) >> 31)) {
+            const int t = (int)tl;
+            const FixDesc f = p.fix[t];
+            if (f.row >= 0) {
+                if (t - f.ts <= PR_LONG) {
+                    const RowIn<T, EPI> in = row_inputs<T, G, false, EPI>(p, io, f.row);
+                    T sum = (T)0;
+                    for (int tt = f.ts; tt < t; ++tt) sum += carry_of<T>(p, agg, tt, io.epoch, ok);
+                    sum += first[t];
+                    row_epilogue<T, G, EPI>(p, io, f.row, sum, true, in, resid, dang);
+                } else {
+                    longt = t;
+                }
+            }
+        }
+        for (uint32_t m = __ballot_sync(FULLMASK, longt >= 0); m; m &= m - 1) {
+            const int t = __shfl_sync(FULLMASK, longt, __ffs(m) - 1);
+            const FixDesc f = p.fix[t];
+            double sum = 0.0;
+            for (int tt = f.ts + lane; tt < t; tt += 32) sum += (double)carry_of<T>(p, agg, tt, io.epoch, ok);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(FULLMASK, sum, off);
+            if (lane == 0) {
+                sum += (double)first[t];
+                const RowIn<T, EPI> in = row_inputs<T, G, false, EPI>(p, io, f.row);
+                row_epilogue<T, G, EPI>(p, io, f.row, (T)sum, true, in, resid, dang);
+            }
+        }
+    }
+    if (!ok) set_status(p.status, (int32_t)GRB_DEVICE_TIMEOUT);
+}
+
 // Phase A over the tiles of this warp (static assignment, next tile's
 // coordinates prefetched), then the rows without nonzeros (EU per thread per
 // step, their loads batched).
@@ -601,7 +691,7 @@ __device__ __forceinline__ void phase_a(const PrParams& p, const TileIO<T, G>& i
 // Phase A with the gathers one tile deep: tile t+nwarps's gathers are issued
 // before tile t's scans and epilogue, so every warp keeps two tiles' loads in
 // flight; tile-start loads run two tiles ahead and the metadata three.
-template <class T, class G, int GMODE, int EPI, bool HOT, int NW>
+template <class T, class G, int GMODE, int EPI, bool HOT, int NW, bool LB = false>
 __device__ __forceinline__ void phase_a_pipe(const PrParams& p, const TileIO<T, G>& io, Acc<T>& resid, Acc<T>& dang,
                                              Smem<T, NW>& sm) {
     const int warp = threadIdx.x >> 5;
@@ -626,11 +716,12 @@ __device__ __forceinline__ void phase_a_pipe(const PrParams& p, const TileIO<T, 
                 f2 = tile_pre(p, t2, meta2);
                 meta2 = t3 < p.ntiles ? __ldg(p.tile_meta + t3) : 0u;
             }
-            tile_finish<T, G, false, EPI>(p, t, f0, v0, io, resid, dang, sm.w[warp]);
+            tile_finish<T, G, false, EPI, LB>(p, t, f0, v0, io, resid, dang, sm.w[warp]);
             f0 = f1;
             f1 = f2;
             v0 = v1;
         }
+        if constexpr (LB) lookback_fixups<T, G, EPI, NW>(p, io, resid, dang);
     }
     empty_rows<T, G, false, EPI, 4>(p, io, resid, dang);
 }
@@ -939,6 +1030,9 @@ template <class T, class G, int BLK, bool HOT, int NST = 0, bool PERS = false, b
 __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS))
     pr_persistent_kernel(const __grid_constant__ PrParams p) {
     constexpr int EPI = PERS ? EPI_PERS : EPI_LEAN;
+    // single pass per body: split rows finished by look-back inside phase A,
+    // one grid barrier per body instead of two (the pipelined hot path)
+    constexpr bool LB = HOT && NST == 0 && !BINS && sizeof(T) == 4;
     __shared__ Smem<T, BLK / 32> sm;
     extern __shared__ int4 hot_raw[];
     // dynamic shared memory: [hot copy (hot_n words)][NST tile stages per
@@ -966,6 +1060,11 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
         else gstore<G>(reinterpret_cast<G*>(p.wbuf[0]), i, (float)q);
         if (p.want_dang && ((p.sinkbits[i >> 5] >> (i & 31)) & 1u)) dang += (double)rv;
     }
+    if constexpr (LB) {
+        // no carry of this launch is published yet
+        unsigned long long* a64 = reinterpret_cast<unsigned long long*>(p.agg);
+        for (int k = blockIdx.x * BLK + threadIdx.x; k < p.ntiles; k += G_ * BLK) a64[k] = 0ull;
+    }
     dang = block_sum_d<BLK>(dang, sm.red2);
     if (threadIdx.x == 0) {
         p.part[2 * blockIdx.x] = 0.0;
@@ -992,6 +1091,7 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
         io.tele_scalar = 1;
         io.hot = reinterpret_cast<const G*>(hot_raw);
         io.hot_n = HOT ? p.hot_n : 0;
+        io.epoch = (uint32_t)it + 1u;
         if constexpr (HOT) {
             // w of this body was written before the last grid barrier
             const int4* src = reinterpret_cast<const int4*>(io.w);
@@ -1006,11 +1106,13 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
             if constexpr (NST > 0)
                 phase_a_tma<T, G, G_W, EPI, HOT, BLK / 32, NST>(p, io, racc, dacc, sm, stages, bars, seq);
             else if constexpr (HOT)
-                phase_a_pipe<T, G, G_W, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
+                phase_a_pipe<T, G, G_W, EPI, HOT, BLK / 32, LB>(p, io, racc, dacc, sm);
             else
                 phase_a<T, G, G_W, false, EPI, HOT, BLK / 32>(p, io, racc, dacc, sm);
-            if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
-            fixups<T, G, false, EPI>(p, io, racc, dacc);
+            if constexpr (!LB) {
+                if (!grid_sync(p.sync, p.status, p.spin_limit, G_, &sm.ok)) return;
+                fixups<T, G, false, EPI>(p, io, racc, dacc);
+            }
         }
         const double resid = block_sum_d<BLK>(racc.value(), sm.red);
         dang = block_sum_d<BLK>(dacc.value(), sm.red2);
