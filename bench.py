@@ -703,7 +703,7 @@ def main():
     peak, peak_kind = _peaks()
     kernel_ms = sum(kernel_ms_steps) / len(kernel_ms_steps)
     achieved = launch_bytes / (kernel_ms * 1e-3) / 1e9
-    # the operation's own minimum (SURVEY-style B = 4m + 20n + 4 per body)
+    # the operation's own minimum per body: B = 4m + 20n + 4 (col_idx once; r_old, r, w_old, w, d once each; the residual)
     min_bytes = ITERS * (4 * m + 20 * n + 4)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": _traffic_per_launch(), "peak_source": peak_kind,
