@@ -8,7 +8,7 @@ Writes OUTDIR/clean_<path>.npy (ranks of clean runs) and OUTDIR/report.json
 (what every planted fault reported).  Faults are planted only through the
 structure check's host-array entry and by overwriting a column index with a
 value just outside [0, n) after the structure was validated -- a case the
-in-kernel checks of this build turn into GRB_INDEX_OUT_OF_BOUNDS.
+in-kernel checks of the bounds-checked library turn into GRB_INDEX_OUT_OF_BOUNDS.
 """
 import json
 import os
