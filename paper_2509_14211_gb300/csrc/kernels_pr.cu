@@ -289,7 +289,7 @@ __device__ __forceinline__ void row_epilogue(const PrParams& p, const TileIO<T, 
         resid.add(abs_c<T>(in.rold - v));
         if (p.want_dang && ((in.sinkword >> (i & 31)) & 1u)) dang.add(v);
         const T q = v / in.dd;
-        if (io.phase32) io.w32_next[i] = (float)q;
+        if (sizeof(G) == 2 && io.phase32) io.w32_next[i] = (float)q;   // only BF16 gathers switch
         else if constexpr (sizeof(T) == 8) reinterpret_cast<double*>(io.w_next)[i] = (double)q;
         else gstore<G>(io.w_next, i, (float)q);
         return;
@@ -332,7 +332,7 @@ __device__ __forceinline__ T gather(const PrParams& p, const TileIO<T, G>& io, i
         return (T)(a + b);
     }
     if (GMODE == G_W) {
-        if (io.phase32) return (T)gload_f<float, NC>(io.w32, j);
+        if (sizeof(G) == 2 && io.phase32) return (T)gload_f<float, NC>(io.w32, j);
         if constexpr (sizeof(T) == 8) return tload<T, NC>(reinterpret_cast<const T*>(io.w), j);
         else return (T)gload_f<G, NC>(io.w, j);
     } else if (GMODE == G_TD) {
