@@ -1138,7 +1138,7 @@ __global__ void __launch_bounds__(BLK, ((HOT || BLK >= 1024) ? 1 : PR_MINBLOCKS)
         // on.  Every CTA sees the same residuals, so all take the same decision.
         const bool stalled = it > 1 && rd > 0.95 * rd_prev;
         rd_prev = rd;
-        if (p.mixed && !phase32 && (rd < p.mixed_switch || stalled) && it < p.iters && rd > p.tol) {
+        if (sizeof(G) == 2 && p.mixed && !phase32 && (rd < p.mixed_switch || stalled) && it < p.iters && rd > p.tol) {
             T* rcur = reinterpret_cast<T*>(p.rbuf[(it - 1) & 1]);
             float* w32 = reinterpret_cast<float*>(p.wbuf32[it & 1]);
             // With uniform dangling the rank sum is invariant (1) in exact
