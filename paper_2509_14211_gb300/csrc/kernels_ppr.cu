@@ -97,13 +97,55 @@ struct Vec<4> {
     }
 };
 
-// Per-lane state of the lane's V slots in the current k-tile.
+// Per-lane state of the lane's V slots in the current k-tile.  It is read
+// or updated only at row ends, so it lives in shared memory (one column per
+// thread: conflict-free) and leaves the registers to the tile loop; only
+// `any` (some slot of the lane is live) stays in a register.  The
+// compensated sums run the same operations as in registers.
+template <int V>
+struct LaneStore {
+    float tb[V][PPR_BLOCK];
+    float rs[V][PPR_BLOCK], rc[V][PPR_BLOCK];   // residual: Kahan sum and compensation
+    float ds[V][PPR_BLOCK], dc[V][PPR_BLOCK];   // dangling mass
+    uint8_t act[V][PPR_BLOCK];
+};
+
+template <int V>
+__device__ __forceinline__ LaneStore<V>& lane_store() {
+    __shared__ LaneStore<V> st;
+    return st;
+}
+
 template <int V>
 struct Lane {
-    bool act[V];
-    float tb[V];
-    Kahan res[V], dang[V];
     bool any;
+    __device__ __forceinline__ bool act(int v) const { return lane_store<V>().act[v][threadIdx.x] != 0; }
+    __device__ __forceinline__ float tb(int v) const { return lane_store<V>().tb[v][threadIdx.x]; }
+    __device__ __forceinline__ static void kahan(float& s_, float& c_, float x) {
+        float s = s_, c = c_;
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+        s_ = s;
+        c_ = c;
+    }
+    __device__ __forceinline__ void res_add(int v, float x) {
+        LaneStore<V>& st = lane_store<V>();
+        kahan(st.rs[v][threadIdx.x], st.rc[v][threadIdx.x], x);
+    }
+    __device__ __forceinline__ void dang_add(int v, float x) {
+        LaneStore<V>& st = lane_store<V>();
+        kahan(st.ds[v][threadIdx.x], st.dc[v][threadIdx.x], x);
+    }
+    __device__ __forceinline__ double res_value(int v) const {
+        const LaneStore<V>& st = lane_store<V>();
+        return (double)st.rs[v][threadIdx.x] - (double)st.rc[v][threadIdx.x];
+    }
+    __device__ __forceinline__ double dang_value(int v) const {
+        const LaneStore<V>& st = lane_store<V>();
+        return (double)st.ds[v][threadIdx.x] - (double)st.dc[v][threadIdx.x];
+    }
 };
 
 __device__ __forceinline__ bool bit_of(const uint32_t* b, int i) { return (__ldg(b + (i >> 5)) >> (i & 31)) & 1u; }
@@ -161,12 +203,12 @@ __device__ __forceinline__ void ppr_row(const PprParams& p, int kt, int i, const
     bool all = true;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        rn.x[v] = (sv[v] + L.tb[v]) + sum[v];
+        rn.x[v] = (sv[v] + L.tb(v)) + sum[v];
         wn.x[v] = rn.x[v] / dd;
-        all = all && L.act[v];
-        if (L.act[v]) {
-            L.res[v].add(fabsf(rold.x[v] - rn.x[v]));
-            if (sink) L.dang[v].add(rn.x[v]);
+        all = all && L.act(v);
+        if (L.act(v)) {
+            L.res_add(v, fabsf(rold.x[v] - rn.x[v]));
+            if (sink) L.dang_add(v, rn.x[v]);
         }
     }
     if (all) {
@@ -175,7 +217,7 @@ __device__ __forceinline__ void ppr_row(const PprParams& p, int kt, int i, const
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            if (L.act[v]) {
+            if (L.act(v)) {
                 p.r_new[o + v] = rn.x[v];
                 p.w_new[o + v] = wn.x[v];
             }
@@ -224,12 +266,12 @@ __device__ __forceinline__ void empty_row(const PprParams& p, int kt, int i, int
     bool all = true;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        rn.x[v] = (sv[v] + L.tb[v]) + 0.f;
+        rn.x[v] = (sv[v] + L.tb(v)) + 0.f;
         wn.x[v] = rn.x[v] / a.dd;
-        all = all && L.act[v];
-        if (L.act[v]) {
-            L.res[v].add(fabsf(a.rold.x[v] - rn.x[v]));
-            if (a.sink) L.dang[v].add(rn.x[v]);
+        all = all && L.act(v);
+        if (L.act(v)) {
+            L.res_add(v, fabsf(a.rold.x[v] - rn.x[v]));
+            if (a.sink) L.dang_add(v, rn.x[v]);
         }
     }
     if (all) {
@@ -238,7 +280,7 @@ __device__ __forceinline__ void empty_row(const PprParams& p, int kt, int i, int
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            if (L.act[v]) {
+            if (L.act(v)) {
                 p.r_new[o + v] = rn.x[v];
                 p.w_new[o + v] = wn.x[v];
             }
@@ -249,13 +291,17 @@ template <int V>
 __device__ __forceinline__ void lane_begin(const PprParams& p, int kt, int lane, Lane<V>& L) {
     const int base = kt * PPR_LANES * V + lane * V;
     L.any = false;
+    LaneStore<V>& st = lane_store<V>();
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        L.act[v] = __ldg(p.active + base + v) != 0;
-        L.tb[v] = __ldg(p.tele_base + base + v);
-        L.res[v] = Kahan();
-        L.dang[v] = Kahan();
-        L.any = L.any || L.act[v];
+        const bool a = __ldg(p.active + base + v) != 0;
+        st.act[v][threadIdx.x] = a ? 1 : 0;
+        st.tb[v][threadIdx.x] = __ldg(p.tele_base + base + v);
+        st.rs[v][threadIdx.x] = 0.f;
+        st.rc[v][threadIdx.x] = 0.f;
+        st.ds[v][threadIdx.x] = 0.f;
+        st.dc[v][threadIdx.x] = 0.f;
+        L.any = L.any || a;
     }
 }
 
@@ -264,8 +310,8 @@ __device__ __forceinline__ void lane_end(int kt, int lane, int warp, const Lane<
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int s = kt * PPR_LANES * V + lane * V + v;
-        sm.res[warp][s] = L.res[v].value();
-        sm.dang[warp][s] = L.dang[v].value();
+        sm.res[warp][s] = L.res_value(v);
+        sm.dang[warp][s] = L.dang_value(v);
     }
 }
 
