@@ -552,15 +552,25 @@ __global__ void ppr_finish_kernel(const __grid_constant__ PprFinish f) {
     }
 }
 
-// Queued slots of one row are adjacent threads, so their zero writes share
-// the row's cache lines.
-__global__ void ppr_init_zero_kernel(const __grid_constant__ PprInitBatch a) {
-    const int64_t total = (int64_t)a.nrows * a.np;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / a.np;
-        const int s = a.slots[q - i * a.np];
-        const int kt = s / a.width, l = s % a.width;
-        const size_t o = ((size_t)kt * a.nrows + (size_t)i) * a.width + l;
+// Zero the queued slots' columns of the current rank / gather buffers.  A
+// block covers rows in groups of 2^lg threads (2^lg >= np, the queued slots,
+// at most PPR_MAX_SLOTS): thread t takes slot t mod 2^lg of row t >> lg, so
+// the queued slots of one row are adjacent threads (their writes share the
+// row's cache lines) and no thread divides by np.
+__global__ void ppr_init_zero_kernel(const __grid_constant__ PprInitBatch a, int lg) {
+    __shared__ long long col[PPR_MAX_SLOTS];   // queued slot k: its k-tile's base + its lane
+    for (int k = threadIdx.x; k < a.np; k += blockDim.x) {
+        const int s = a.slots[k];
+        col[k] = (long long)(s / a.width) * a.nrows * a.width + (s % a.width);
+    }
+    __syncthreads();
+    const int k = threadIdx.x & ((1 << lg) - 1);
+    if (k >= a.np) return;
+    const int rows_per_pass = blockDim.x >> lg;
+    const long long c = col[k];
+    for (long long i = (long long)blockIdx.x * rows_per_pass + (threadIdx.x >> lg); i < a.nrows;
+         i += (long long)gridDim.x * rows_per_pass) {
+        const size_t o = (size_t)(c + i * a.width);
         a.r[o] = 0.f;
         a.w[o] = 0.f;
     }
@@ -658,7 +668,10 @@ cudaError_t launch_ppr_finish(cudaStream_t st, const PprFinish& f) {
 
 cudaError_t launch_ppr_init_batch(cudaStream_t st, const PprInitBatch& a) {
     if (a.np <= 0) return cudaSuccess;
-    ppr_init_zero_kernel<<<grid_1d((int64_t)a.nrows * a.np), 256, 0, st>>>(a);
+    if (a.np > PPR_MAX_SLOTS) return cudaErrorInvalidValue;   // queued entries are distinct slots
+    int lg = 0;
+    while ((1 << lg) < a.np) ++lg;
+    ppr_init_zero_kernel<<<grid_1d((int64_t)a.nrows << lg), 256, 0, st>>>(a, lg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ppr_init_seed_kernel<<<a.np, 256, 0, st>>>(a);
