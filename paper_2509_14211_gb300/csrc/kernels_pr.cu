@@ -19,11 +19,12 @@
 // loop.  Warps are independent: per-lane segmented sums go to the warp's
 // shared-memory slice, and a warp-wide segmented scan joins rows split across
 // lanes (ballots number the rows and mark where segments start; only the
-// carried values are shuffled).  Rows split across tiles are finished in a second
-// phase after a grid barrier, from per-tile carries (phase A writes them,
-// phase B adds them up in a fixed order); there are no cross-warp waits
-// inside a phase, and every barrier wait is bounded.  All reductions have a
-// fixed order, so results are bit-reproducible.
+// carried values are shuffled).  Rows split across tiles are finished from
+// per-tile carries (phase A writes them, phase B adds them up in a fixed
+// order): after a grid barrier, or -- in the pipelined persistent loop --
+// by look-back over carries the other warps published, each tagged with the
+// body, so that a body has a single grid barrier.  Every wait is bounded.
+// All reductions have a fixed order, so results are bit-reproducible.
 //
 // Three epilogue flavours, compiled separately so that the loop's per-row
 // code carries no run-time configuration checks: LEAN (the PageRank loop:
@@ -1015,8 +1016,9 @@ __global__ void __launch_bounds__(PR_BLOCK, PR_MINBLOCKS) pr_iter_kernel(const _
 
 // Whole loop in one launch: prologue (w_0 = r_0 ./ d and the dangling mass of
 // r_0), then bodies while the condition holds; each body is phase A,
-// barrier, phase B, barrier, and every CTA folds the same partials in the
-// same order, so all CTAs take the same loop decision.
+// barrier, phase B, barrier (single pass, LB: phase A with the look-back
+// fixups, barrier), and every CTA folds the same partials in the same
+// order, so all CTAs take the same loop decision.
 //
 // HOT (one CTA of BLK = PR_HOT_BLOCK threads per SM): at the start of each body the
 // CTA copies w[0, hot_n) into shared memory and serves gathers of those
