@@ -95,3 +95,15 @@ def test_block_diagonal_edges_offsets_each_graph(lib):
         lo, hi = vptr[k], vptr[k + 1]
         inside = (src >= lo) & (src < hi)
         assert np.all((dst[inside] >= lo) & (dst[inside] < hi))   # no edge leaves its block
+
+
+def test_binding_constants_match_the_header():
+    """The binding's size limits are the header's."""
+    import paper_2509_14211_gb300 as grb
+
+    with open(os.path.join(ROOT, "include", "grb.h")) as f:
+        text = f.read()
+    m = re.search(r"#define GRB_FUSED_INDEX_LIMIT (\d+)LL", text)
+    assert m and int(m.group(1)) == grb.GRB_FUSED_INDEX_LIMIT == (1 << 31) - (1 << 24)
+    m = re.search(r"#define GRB_HOT_BYTES_MAX (\d+)", text)
+    assert m and int(m.group(1)) == grb.GRB_HOT_BYTES_MAX
